@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the nested Monte Carlo hot path: path-steps/s on the 5-asset max-call.
+
+One step = the whole hot path over one batch: for S0 in {90, 100, 110}, the Ibanez-Zapatero
+fit (5 boundaries x J=1024 Korobov points per date, N1 = 1e5 inner paths per continuation
+estimate, device Newton to |f| < 1e-6 or the x tolerance, FP64 quadratic regression, 8 fitted
+dates) and the final pricing with 1e6 paths (plus the FP64 re-run of the pricing that states
+the FP32 error).  value = inner + pricing path-steps actually simulated / device time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own replica of the step (independent options, different
+seeds; no collective on the data path) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from bap_workloads import IZParams, spec_max_call  # noqa: E402
+
+S0S = (90.0, 100.0, 110.0)
+J_FULL, N1_FULL, N_PRICE = 1024, 100_000, 1_000_000
+METRIC = "nested-MC path-steps/s (5-asset max-call)"
+WORKLOAD = "5-asset max-call Bermudan, I&Z, rho=0.3, J=1024 Korobov, N1=1e5, 9 dates, N=1e6"
+# CPU sample of the same workload for the oracle (about 10-30 s of CPU work)
+CPU_J, CPU_N1, CPU_NPRICE = 64, 4000, 100_000
+
+
+def alg_ops_per_path_step(d: int = 5, degree: int = 2) -> dict:
+    """Algorithmic 32-bit lane operations of one path-step of the I&Z max-call path:
+    Philox4x32-10: ceil(d/4) calls x 10 rounds x (2 wide multiplies + 4 xor);
+    Box-Muller: ceil(d/2) pairs x (4 uniform ops + 4 MUFU + 4 FP32);
+    mixing d(d+1)/2 FMA; log-space step 2d; prices d exp2 (MUFU); argmax 2(d-1);
+    payoff 2; boundary: (d-1) selects + n_coef FMA + 1 compare."""
+    s = d - 1
+    n_coef = 1 + (s if degree >= 1 else 0) + (s * (s + 1) // 2 if degree >= 2 else 0)
+    calls = (d + 3) // 4
+    pairs = (d + 1) // 2
+    ops = {
+        "philox_int": calls * 10 * 6,
+        "uniform_int": pairs * 4,
+        "box_muller_fp32": pairs * 4,
+        "mufu": pairs * 4 + d,
+        "mix_fma": d * (d + 1) // 2,
+        "step_fp32": 2 * d,
+        "argmax_payoff": 2 * (d - 1) + 2,
+        "rule": s + n_coef + 1,
+    }
+    ops["total"] = sum(ops.values())
+    return ops
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args) -> None:
+    """The oracle (plain FP64 C + numpy) on the host cores, same metric and unit."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    spec = spec_max_call(5, 100.0, rho=0.3)
+    params = IZParams(J=CPU_J, N1=CPU_N1, degree=2, seed=0)
+
+    def one():
+        t = time.perf_counter()
+        rules, diag = oracle.iz_fit(spec, params, n_threads=cores)
+        res = oracle.price(spec, rules, CPU_NPRICE, 1, n_threads=cores)
+        el = time.perf_counter() - t
+        return sum(d["steps"] for d in diag.values()) + res["path_steps"], el
+
+    for _ in range(args.warmup):
+        one()
+    steps = secs = 0.0
+    for _ in range(args.steps):
+        s, e = one()
+        steps += s
+        secs += e
+    value = steps / secs
+    sample = (f"oracle I&Z fit of the 5-asset max-call (rho=0.3, S0=100, 9 dates) at J={CPU_J}, "
+              f"N1={CPU_N1}, all 8 fitted dates, plus {CPU_NPRICE} pricing paths; FP64; OpenMP "
+              f"over items; per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "path-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded CPU sample, see cpu_baseline)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline() -> dict:
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    spec = spec_max_call(5, 100.0, rho=0.3)
+    params = IZParams(J=CPU_J, N1=CPU_N1, degree=2, seed=0)
+    t = time.perf_counter()
+    rules, diag = oracle.iz_fit(spec, params, n_threads=cores)
+    res = oracle.price(spec, rules, CPU_NPRICE, 1, n_threads=cores)
+    el = time.perf_counter() - t
+    steps = sum(d["steps"] for d in diag.values()) + res["path_steps"]
+    return {"value": steps / el, "unit": "path-steps/s", "cores": cores, "kind": "oracle",
+            "sample": (f"I&Z fit of the 5-asset max-call (rho=0.3, S0=100, 9 dates) at "
+                       f"J={CPU_J}, N1={CPU_N1}, 8 fitted dates + {CPU_NPRICE} pricing paths "
+                       f"({steps} path-steps in {el:.1f} s); FP64 C with OpenMP over items")}
+
+
+def run_ours(args) -> None:
+    import torch
+    import paper_0805_1827_gb300 as bap
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    stream = torch.cuda.current_stream()
+    J = args.J or J_FULL
+    N1 = args.N1 or N1_FULL
+    opts = [bap.Option(spec_max_call(5, s0, rho=0.3), stream=stream.cuda_stream) for s0 in S0S]
+    params = IZParams(J=J, N1=N1, degree=2, seed=1000 * rank + 1)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(seed_price: int):
+        steps = launches = path_launches = 0
+        kms = 0.0
+        res = []
+        for o in opts:
+            o.fit_boundary(params)
+            r = o.price(N_PRICE, seed_price)
+            steps += r["fit_path_steps"] + r["path_steps"]
+            launches += r["kernel_launches"]
+            path_launches += r["path_launches"]
+            kms += r["path_kernel_ms"]
+            res.append(r)
+        return steps, launches, path_launches, kms, res
+
+    for i in range(args.warmup):
+        step(7)
+    for o in opts:
+        o.set_profiling(True)
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times, tot_steps, tot_launch, tot_plaunch, tot_kms = [], 0, 0, 0, 0.0
+    last = None
+    for i in range(args.steps):
+        flush.zero_()                       # evict L2 (129 MB) between timed steps
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s, l, pl, kms, res = step(7)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        tot_steps += s
+        tot_launch += l
+        tot_plaunch += pl
+        tot_kms += kms
+        last = res
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    for o in opts:
+        o.set_profiling(False)
+    elapsed_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms, float(tot_steps)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        elapsed_all, steps_all = float(tmax[0]), float(t[1])
+    else:
+        elapsed_all, steps_all = elapsed_ms, float(tot_steps)
+    value = steps_all / (elapsed_all / 1e3)
+
+    # end to end through the public API with host buffers: create (model H2D), fit, price (D2H)
+    e2e_steps, e2e_secs = 0, 0.0
+    h2d = d2h = 0
+    for i in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s0 in S0S:
+            spec = spec_max_call(5, s0, rho=0.3)
+            o = bap.Option(spec)
+            o.fit_boundary(params)
+            r = o.price(N_PRICE, 7)
+            o.close()
+            e2e_steps += r["fit_path_steps"] + r["path_steps"]
+            if i == 0:
+                h2d += 8 * (3 * spec.d + spec.d * spec.d)
+                d2h += 8 * 16   # result struct plus the fit's and pricing's status reads
+        e2e_secs += time.perf_counter() - t0
+    e2e_value = e2e_steps / e2e_secs
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    ops = alg_ops_per_path_step(5, 2)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * sm_max * 1e6    # lane-ops/s at max clock
+    achieved = (tot_steps * ops["total"]) / (tot_kms / 1e3) if tot_kms > 0 else None
+    roof = {"bound": "alu", "kernel": "path_kernel<5,IZ,float>",
+            "achieved": achieved / 1e12 if achieved else None,
+            "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": (achieved / peak_ops) if achieved else None,
+            "traffic": None,
+            "ops_per_path_step": ops["total"],
+            "path_steps_per_s_in_kernel": tot_steps / (tot_kms / 1e3) if tot_kms > 0 else None,
+            "peak_basis": (f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {sm_max:.0f} "
+                           "MHz (issue-slot peak; MEASURED_PEAKS sm_max_mhz)")}
+    line = {
+        "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "options_per_step": len(S0S), "J": J, "N1": N1,
+                   "N_price": N_PRICE, "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": tot_launch,
+        "roofline": roof,
+        "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
+                                  "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
+                   for s0, r in zip(S0S, last)},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
+    ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * bap.h -- C ABI of the GB300 (sm_103a) nested Monte Carlo Bermudan/American option library.
+ *
+ * Method: Doan, Gaikwad, Bossy, Baude & Stokes-Rees, "Parallel Pricing Algorithms for
+ * Multi-Dimensional Bermudan/American Options using Monte Carlo methods", INRIA RR-6530 (2008):
+ *   - Section 2 (Algorithm 1): Ibanez-Zapatero exercise-boundary search.  At every exercise date,
+ *     backward in time, boundary points solve the matched condition P_t(S*) = I(S*) (Eq. 1) by
+ *     Newton iterations on nested Monte Carlo continuation values; a polynomial boundary is
+ *     regressed on the points; the price is a Monte Carlo mean under the fitted boundaries.
+ *   - Section 3 (Algorithm 2): Picazo classification Monte Carlo.  Training points are labelled by
+ *     the sign of (exercise value - continuation value) and a boosted classifier F_t with
+ *     sign F_t = sign beta(t, .) gives the stopping rule tau = min{t_m : F_{t_m}(S) > 0}.
+ *
+ * Conventions for every call:
+ *   - Pointers are HOST pointers unless a parameter says otherwise.  The caller owns every input
+ *     array; the library copies what it keeps before the call returns.
+ *   - The library owns the handles and all device memory they hold.  Results go to caller-owned
+ *     host memory.
+ *   - Errors come back as a bap_status; nothing throws or exits across the ABI.  A thread-local
+ *     message for the last failure is available from bap_last_error().
+ *   - A bap_option is not thread safe; use one thread per option (or serialize).  bap_server is
+ *     thread safe for bap_submit and bap_poll.
+ *   - Everything runs on the CUDA device current at bap_create, on the option's stream (default:
+ *     a stream the library creates; see bap_set_stream).  Calls that return results synchronize
+ *     that stream.
+ *   - There is no CPU fallback: without a CUDA device every compute call returns BAP_ECUDA.
+ */
+#ifndef BAP_H
+#define BAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BAP_OK = 0,
+    BAP_EINVAL = 1,     /* bad argument (message in bap_last_error) */
+    BAP_ENOMEM = 2,     /* device or host allocation failed */
+    BAP_ECUDA = 3,      /* CUDA error, or no CUDA device */
+    BAP_ENOCONV = 4,    /* fit finished; some Newton points hit max_iter (result still valid) */
+    BAP_ENOTREADY = 5,  /* bap_poll: the request is not finished yet */
+    BAP_EBUSY = 6,      /* bap_submit: admission refused (memory budget or slots full) */
+    BAP_ETIMEOUT = 7,   /* a bounded device wait gave up */
+    BAP_ESTATE = 8      /* call out of order, e.g. bap_price before a fit */
+} bap_status;
+
+/* Payoff Phi(S) at an exercise date (Section 2.2 defines the max-call). */
+typedef enum {
+    BAP_MAX_CALL = 0,   /* (max_i S_i - K)^+ */
+    BAP_BASKET_PUT = 1, /* (K - sum_i w_i S_i)^+ ; with d = 1 the vanilla put */
+    BAP_GEO_CALL = 2    /* (prod_i S_i^{w_i} - K)^+ */
+} bap_payoff;
+
+typedef enum { BAP_METHOD_IZ = 0, BAP_METHOD_CMC = 1 } bap_method;
+
+#define BAP_MAX_D 10           /* largest number of assets */
+#define BAP_MAX_DATES 64       /* largest number of exercise dates */
+#define BAP_MAX_STUMPS 256     /* largest number of boosted stumps per date */
+
+/* Market model (Section 2.2 and 3.2): d assets following correlated geometric Brownian motion
+ * under the risk-neutral measure, dS_i/S_i = (r - delta_i) dt + sigma_i dW_i, corr(dW) = rho. */
+typedef struct bap_model {
+    int d;                    /* 1..BAP_MAX_D */
+    const double *S0;         /* d spot prices, > 0 */
+    const double *sigma;      /* d volatilities, > 0 */
+    const double *delta;      /* d dividend yields */
+    const double *rho;        /* d*d row-major correlation: symmetric, unit diagonal, positive
+                                 definite (checked by an FP64 Cholesky factorisation) */
+    double r;                 /* constant interest rate */
+    double K;                 /* strike, > 0 */
+    double T;                 /* maturity, > 0 */
+    int n_dates;              /* N_T exercise dates, 1..BAP_MAX_DATES */
+    const double *dates;      /* NULL: t_k = k T / n_dates; else n_dates increasing values in
+                                 (0, T] with dates[n_dates-1] == T */
+    int payoff;               /* bap_payoff */
+    const double *weights;    /* NULL: 1/d each; else d basket weights (basket put, geo call) */
+} bap_model;
+
+/* Ibanez-Zapatero parameters (Section 2.2-2.3, Algorithm 1). */
+typedef struct bap_iz_params {
+    int J;                    /* boundary points per boundary and date (Korobov lattice in the
+                                 d-1 other assets; d = 1: J replicate points), 1..8192 */
+    int64_t N1;               /* inner paths per continuation estimate, >= 1 */
+    double f_tol;             /* stop when |Phi(x) - C(x)| < f_tol (e.g. 1e-6) */
+    double x_tol;             /* or when the step or bracket is <= x_tol * max(1, |x|) (e.g. 1e-5) */
+    int max_iter;             /* Newton iterations per point, 1..200 (e.g. 50) */
+    int degree;               /* boundary polynomial degree 0..2 (d = 1 uses 0) */
+    uint64_t seed;
+    int fixed_point;          /* 1: the paper's literal iteration x <- Phi^-1(C(x)) with |dx| <
+                                 fp_eps (Section 2.4); 0: safeguarded Newton */
+    double fp_eps;
+} bap_iz_params;
+
+/* Picazo CMC parameters (Section 3.2-3.3, Algorithm 2). */
+typedef struct bap_cmc_params {
+    int J;                    /* training points per date, 2..8192 */
+    int64_t N2;               /* inner paths per training point, >= 1 */
+    int n_stumps;             /* boosting rounds per date, 1..BAP_MAX_STUMPS */
+    uint64_t seed;
+} bap_cmc_params;
+
+typedef struct bap_result {
+    double price;             /* Monte Carlo mean of the discounted payoff at tau */
+    double se;                /* standard error sqrt(var / n_paths) */
+    double var;               /* unbiased sample variance of the discounted payoff */
+    double ci95;              /* 1.96 * se */
+    int64_t n_paths;
+    int64_t path_steps;       /* pricing path-steps actually simulated */
+    double fp64_delta;        /* price(FP32 paths) - price(FP64 paths), same counters and rules */
+    int n_noconv;             /* boundary points that hit max_iter in the last fit */
+    int n_noroot;             /* boundary points without a sign change (left out of the fit) */
+    int64_t fit_path_steps;   /* inner path-steps of the last fit */
+    double fit_ms;            /* device time of the last fit (CUDA events) */
+    double price_ms;          /* device time of the pricing launch */
+    int64_t kernel_launches;  /* kernels the library launched for the last fit and this pricing */
+    int64_t path_launches;    /* of which path-kernel launches */
+    double path_kernel_ms;    /* summed CUDA-event time of those path-kernel launches (only with
+                                 bap_set_profiling on; else 0); the FP64 check of
+                                 bap_price is not timed */
+} bap_result;
+
+typedef struct bap_option bap_option;
+typedef struct bap_server bap_server;
+
+/* Create an option: copies and validates the model (FP64 Cholesky of rho on the device) and
+ * uploads it.  *out is set on success.  Errors: EINVAL (bad model), ENOMEM, ECUDA. */
+bap_status bap_create(const bap_model *model, bap_option **out);
+
+/* Run the option's work on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream). */
+bap_status bap_set_stream(bap_option *opt, void *cuda_stream);
+
+/* 1: time every path-kernel launch with a CUDA event pair on the option's stream (reported in
+ * bap_result.path_kernel_ms); 0 (default): no per-launch events. */
+bap_status bap_set_profiling(bap_option *opt, int on);
+
+/* Ibanez-Zapatero fit (Algorithm 1 without [mc]): for m = N_T-1..1, boundary points by
+ * device Newton on N1-path continuation estimates, then an FP64 least-squares boundary per
+ * (date, boundary).  The fitted rule stays on the device.  Returns OK or ENOCONV. */
+bap_status bap_fit_boundary(bap_option *opt, const bap_iz_params *params);
+
+/* CMC fit (Algorithm 2 without [mc]): for m = N_T-1..1, J training points from the law of
+ * S_{t_m}, labels from N2-path continuation estimates, AdaBoost stumps on the device. */
+bap_status bap_fit_classifier(bap_option *opt, const bap_cmc_params *params);
+
+/* Final pricing ([mc]): n_paths outer paths from S0 under the fitted rule (or, before any fit,
+ * exercise at maturity only).  Also reports fp64_delta.  n_paths in 2..2^40. */
+bap_status bap_price(bap_option *opt, int64_t n_paths, uint64_t seed, bap_result *out);
+
+/* Rule checkpoint.  Export: with buf == NULL sets *len to the number of doubles needed; else
+ * writes min(*len, needed) doubles and sets *len to needed.  Layout (doubles): [kind, n_dates,
+ * n_bnd, degree, n_coef, max_stumps, fitted[n_dates+1], then I&Z coef[(n_dates+1)*n_bnd*n_coef]
+ * or CMC per date (n_dates+1) x max_stumps x (feat, thr, pol, alpha) plus n_stumps[n_dates+1]].
+ * Import accepts the same layout (kind 0 = exercise at maturity only). */
+bap_status bap_export_rules(const bap_option *opt, double *buf, size_t *len);
+bap_status bap_import_rules(bap_option *opt, const double *buf, size_t len);
+
+/* Per boundary point (I&Z) or training point (CMC) diagnostics of date m from the last fit:
+ * n_items rows of x (I&Z: the boundary point along the pivot; CMC: Phi - C), iterations and
+ * status (0 ok, 1 no convergence, 2 no root).  *n_items in: capacity, out: count. */
+bap_status bap_fit_points(const bap_option *opt, int m, int *n_items, double *x, int *iters,
+                          int *status);
+
+/* Continuation sums for caller-given start points under the option's current rule (debug and
+ * parity hook).  For each item i: paths n = 0..N-1 from S_{t_m} = starts[i*d..] with counter
+ * item item_ids[i] under stream `purpose` (1 I&Z, 2 CMC).  sums[3i..3i+2] = sum of discounted
+ * payoffs, sum of squares, sum of pathwise derivatives w.r.t. starts[i*d + pivots[i]] (pivots
+ * may be NULL); steps[i] = path-steps.  1 <= m < n_dates. */
+bap_status bap_debug_continuation(bap_option *opt, int m, int purpose, uint64_t seed,
+                                  int n_items, const int *item_ids, const int *pivots,
+                                  const double *starts, int64_t N, double *sums, int64_t *steps);
+
+/* Per-path exercise date (n_dates+1 = never) and discounted payoff of one item (parity hook). */
+bap_status bap_debug_paths(bap_option *opt, int m, int purpose, uint64_t seed, int item_id,
+                           const double *start, int64_t N, int *tau, double *disc_phi);
+
+/* Raw Philox4x32-10 words and the Box-Muller normals of the counters (n, w1, 4*step + c),
+ * n = 0..count-1, under key (seed, purpose, m) (parity hook; no option needed).  words:
+ * count * 4 * ceil(d/4) uint32 (may be NULL); z: count * d doubles converted from the FP32
+ * normals (may be NULL). */
+bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_t step, int d,
+                         int64_t count, uint32_t *words, double *z);
+
+/* Release an option and its device memory (NULL is ignored). */
+void bap_destroy(bap_option *opt);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bap_last_error(void);
+
+/* Library version string. */
+const char *bap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAP_H */

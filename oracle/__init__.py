@@ -340,7 +340,7 @@ def p2_merit(J: int, g) -> float:
 def korobov_generator(J: int, s: int) -> int:
     """The Korobov multiplier a in [1, J) coprime to J minimising P_2 of (1, a, .., a^{s-1});
     values within 1e-9 (relative) of the minimum tie, and the smallest a wins."""
-    if s <= 1:
+    if s <= 1 or J <= 2:
         return 1
     best_a, vals = 1, {}
     for a in range(1, J):

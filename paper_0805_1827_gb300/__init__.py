@@ -1,0 +1,225 @@
+"""Python binding of the GB300 nested Monte Carlo Bermudan/American option library (libbap.so).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.  The
+binding loads the in-tree ``_build/libbap.so`` and raises if it is missing; there is no CPU
+fallback.  Names follow ``include/bap.h``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH, build, needs_build   # noqa: F401
+
+BAP_OK, BAP_EINVAL, BAP_ENOMEM, BAP_ECUDA, BAP_ENOCONV = 0, 1, 2, 3, 4
+BAP_ENOTREADY, BAP_EBUSY, BAP_ETIMEOUT, BAP_ESTATE = 5, 6, 7, 8
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENOTREADY",
+                6: "EBUSY", 7: "ETIMEOUT", 8: "ESTATE"}
+PAYOFF_CODE = {"max_call": 0, "basket_put": 1, "geo_call": 2}
+PURPOSE_IZ, PURPOSE_CMC, PURPOSE_TRAIN, PURPOSE_PRICE = 1, 2, 3, 4
+MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
+
+EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_fit_boundary", "bap_fit_classifier",
+            "bap_price", "bap_export_rules", "bap_import_rules", "bap_fit_points",
+            "bap_debug_continuation", "bap_debug_paths", "bap_debug_rng", "bap_destroy",
+            "bap_last_error", "bap_version"]
+
+
+class BapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Model(C.Structure):
+    _fields_ = [("d", C.c_int), ("S0", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("delta", C.POINTER(C.c_double)), ("rho", C.POINTER(C.c_double)),
+                ("r", C.c_double), ("K", C.c_double), ("T", C.c_double), ("n_dates", C.c_int),
+                ("dates", C.POINTER(C.c_double)), ("payoff", C.c_int),
+                ("weights", C.POINTER(C.c_double))]
+
+
+class _IZ(C.Structure):
+    _fields_ = [("J", C.c_int), ("N1", C.c_int64), ("f_tol", C.c_double), ("x_tol", C.c_double),
+                ("max_iter", C.c_int), ("degree", C.c_int), ("seed", C.c_uint64),
+                ("fixed_point", C.c_int), ("fp_eps", C.c_double)]
+
+
+class _CMC(C.Structure):
+    _fields_ = [("J", C.c_int), ("N2", C.c_int64), ("n_stumps", C.c_int), ("seed", C.c_uint64)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("price", C.c_double), ("se", C.c_double), ("var", C.c_double),
+                ("ci95", C.c_double), ("n_paths", C.c_int64), ("path_steps", C.c_int64),
+                ("fp64_delta", C.c_double), ("n_noconv", C.c_int), ("n_noroot", C.c_int),
+                ("fit_path_steps", C.c_int64), ("fit_ms", C.c_double), ("price_ms", C.c_double),
+                ("kernel_launches", C.c_int64), ("path_launches", C.c_int64),
+                ("path_kernel_ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbap.so (built on first use if the CUDA toolkit is present)."""
+    global _lib
+    if _lib is None:
+        if needs_build():
+            build()
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libbap.so not found at {_LIB_PATH}; run paper_0805_1827_gb300.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp = C.c_void_p
+        dp, ip, i64p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
+        L.bap_create.argtypes = [C.POINTER(_Model), C.POINTER(vp)]
+        L.bap_set_stream.argtypes = [vp, vp]
+        L.bap_set_profiling.argtypes = [vp, C.c_int]
+        L.bap_fit_boundary.argtypes = [vp, C.POINTER(_IZ)]
+        L.bap_fit_classifier.argtypes = [vp, C.POINTER(_CMC)]
+        L.bap_price.argtypes = [vp, C.c_int64, C.c_uint64, C.POINTER(_Result)]
+        L.bap_export_rules.argtypes = [vp, dp, C.POINTER(C.c_size_t)]
+        L.bap_import_rules.argtypes = [vp, dp, C.c_size_t]
+        L.bap_fit_points.argtypes = [vp, C.c_int, ip, dp, ip, ip]
+        L.bap_debug_continuation.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, C.c_int, ip, ip, dp,
+                                             C.c_int64, dp, i64p]
+        L.bap_debug_paths.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, C.c_int64,
+                                      ip, dp]
+        L.bap_debug_rng.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_int,
+                                    C.c_int64, C.POINTER(C.c_uint32), dp]
+        L.bap_destroy.argtypes = [vp]
+        L.bap_destroy.restype = None
+        L.bap_last_error.restype = C.c_char_p
+        L.bap_version.restype = C.c_char_p
+        for name in EXPORTED:
+            if name not in ("bap_destroy", "bap_last_error", "bap_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int, allow=(BAP_OK,)) -> int:
+    if st not in allow:
+        raise BapError(st, lib().bap_last_error().decode())
+    return st
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Option:
+    """An option on the device: bap_create / bap_fit_boundary / bap_fit_classifier / bap_price."""
+
+    def __init__(self, spec, stream: Optional[int] = None):
+        L = lib()
+        self.spec = spec
+        self._keep = [_f64(spec.S0), _f64(spec.sigma), _f64(spec.delta), _f64(spec.rho)]
+        dates = None if spec.dates is None else _f64(spec.dates)
+        w = None if spec.weights is None else _f64(spec.weights)
+        self._keep += [dates, w]
+        m = _Model(spec.d, _dp(self._keep[0]), _dp(self._keep[1]), _dp(self._keep[2]),
+                   _dp(self._keep[3]), spec.r, spec.K, spec.T, spec.n_dates,
+                   None if dates is None else _dp(dates), PAYOFF_CODE[spec.payoff],
+                   None if w is None else _dp(w))
+        h = C.c_void_p()
+        _check(L.bap_create(C.byref(m), C.byref(h)))
+        self.h = h
+        if stream is not None:
+            _check(L.bap_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: int):
+        _check(lib().bap_set_stream(self.h, C.c_void_p(stream)))
+
+    def set_profiling(self, on: bool):
+        _check(lib().bap_set_profiling(self.h, 1 if on else 0))
+
+    def fit_boundary(self, p) -> int:
+        c = _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point, p.fp_eps)
+        return _check(lib().bap_fit_boundary(self.h, C.byref(c)), (BAP_OK, BAP_ENOCONV))
+
+    def fit_classifier(self, p) -> int:
+        c = _CMC(p.J, p.N2, p.n_stumps, p.seed)
+        return _check(lib().bap_fit_classifier(self.h, C.byref(c)))
+
+    def price(self, n_paths: int, seed: int) -> dict:
+        r = _Result()
+        _check(lib().bap_price(self.h, n_paths, seed, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in _Result._fields_}
+
+    def export_rules(self) -> np.ndarray:
+        n = C.c_size_t(0)
+        _check(lib().bap_export_rules(self.h, None, C.byref(n)))
+        buf = np.zeros(n.value)
+        _check(lib().bap_export_rules(self.h, _dp(buf), C.byref(n)))
+        return buf
+
+    def import_rules(self, buf) -> None:
+        buf = _f64(buf)
+        _check(lib().bap_import_rules(self.h, _dp(buf), buf.size))
+
+    def fit_points(self, m: int):
+        n = C.c_int(0)
+        _check(lib().bap_fit_points(self.h, m, C.byref(n), None, None, None))
+        x = np.zeros(n.value)
+        it = np.zeros(n.value, dtype=np.int32)
+        st = np.zeros(n.value, dtype=np.int32)
+        _check(lib().bap_fit_points(self.h, m, C.byref(n), _dp(x), _ip(it), _ip(st)))
+        return x, it, st
+
+    def debug_continuation(self, m: int, purpose: int, seed: int, item_ids, starts, N: int,
+                           pivots=None):
+        starts = _f64(np.atleast_2d(starts))
+        n = starts.shape[0]
+        ids = np.ascontiguousarray(item_ids, dtype=np.int32)
+        piv = None if pivots is None else np.ascontiguousarray(pivots, dtype=np.int32)
+        sums = np.zeros((n, 3))
+        steps = np.zeros(n, dtype=np.int64)
+        _check(lib().bap_debug_continuation(self.h, m, purpose, seed, n, _ip(ids),
+                                            None if piv is None else _ip(piv), _dp(starts), N,
+                                            _dp(sums), steps.ctypes.data_as(C.POINTER(C.c_int64))))
+        return sums, steps
+
+    def debug_paths(self, m: int, purpose: int, seed: int, item_id: int, start, N: int):
+        start = _f64(start)
+        tau = np.zeros(N, dtype=np.int32)
+        phi = np.zeros(N)
+        _check(lib().bap_debug_paths(self.h, m, purpose, seed, item_id, _dp(start), N, _ip(tau),
+                                     _dp(phi)))
+        return tau, phi
+
+
+def debug_rng(seed: int, purpose: int, m: int, w1: int, step: int, d: int, count: int):
+    """Raw Philox words (count x ceil(d/4) x 4) and FP32 Box-Muller normals (count x d)."""
+    nc = (d + 3) // 4
+    words = np.zeros((count, nc, 4), dtype=np.uint32)
+    z = np.zeros((count, d))
+    _check(lib().bap_debug_rng(seed, purpose, m, w1, step, d, count,
+                               words.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(z)))
+    return words, z
+
+
+def version() -> str:
+    return lib().bap_version().decode()

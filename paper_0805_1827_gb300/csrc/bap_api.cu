@@ -1,0 +1,950 @@
+// bap_api.cu -- host side of the C ABI declared in include/bap.h.
+//
+// The host validates arguments, owns device buffers and enqueues kernels on the option's
+// stream.  Every step of the method (Cholesky, lattice, Newton iterations, regression,
+// training points, boosting, pricing) runs in device kernels; the host reads back only the
+// results a call returns.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "bap_fit.cuh"
+#include "bap_path.cuh"
+
+using namespace bap;
+
+namespace {
+
+thread_local std::string g_err;
+
+bap_status fail(bap_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CU(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? BAP_ENOMEM : BAP_ECUDA,            \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        bap_status s_ = (expr);            \
+        if (s_ != BAP_OK) return s_;       \
+    } while (0)
+
+// A device buffer that grows on demand.
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    bap_status reserve(size_t bytes) {
+        if (bytes <= n) return BAP_OK;
+        if (p) { cudaFree(p); p = nullptr; n = 0; }
+        cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(BAP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        }
+        n = bytes < 256 ? 256 : bytes;
+        return BAP_OK;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+constexpr int kBlock = 256;
+
+struct FnInfo {
+    int blocks_per_sm = 0;
+    size_t smem_set = 0;
+};
+std::mutex g_fn_mu;
+std::unordered_map<const void*, FnInfo> g_fn;
+
+const void* path_fn(int D, int rule, bool fp64) {
+    switch (D) {
+        case 1: return path_kernel_fn<1>(rule, fp64);
+        case 2: return path_kernel_fn<2>(rule, fp64);
+        case 3: return path_kernel_fn<3>(rule, fp64);
+        case 4: return path_kernel_fn<4>(rule, fp64);
+        case 5: return path_kernel_fn<5>(rule, fp64);
+        case 6: return path_kernel_fn<6>(rule, fp64);
+        case 7: return path_kernel_fn<7>(rule, fp64);
+        case 8: return path_kernel_fn<8>(rule, fp64);
+        case 9: return path_kernel_fn<9>(rule, fp64);
+        case 10: return path_kernel_fn<10>(rule, fp64);
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+
+struct bap_option {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    // model (host copies)
+    int d = 0, n_dates = 0, payoff = 0;
+    double r = 0, K = 0, T = 0;
+    DevModel hm{};                // host copy after device set-up
+    DevBuf dmodel;
+    // rule
+    int rule_kind = R_NONE;
+    int n_bnd = 1, degree = 0, n_coef = 1;
+    int max_stumps = 0, rec_len = 0;
+    DevBuf fitted;                // int[n_dates+1]
+    DevBuf coef64, coef_f, coef_d;
+    DevBuf n_stumps, feat, thr, pol, alpha, rec_f, rec_d;
+    // fit state and scratch
+    int method = -1;              // last fit: 0 I&Z, 1 CMC
+    int n_items = 0;
+    DevBuf start, state, pivot, ctr_item, active0, active1, counts, work, partial,
+        partial_steps, done, total_steps, korobov_a, merit, label_y, label, sorted_v, sorted_i,
+        err, out_sums, out_steps, trace_tau, trace_phi, diag_x, diag_it, diag_st, stat_counts,
+        one;
+    int last_noconv = 0, last_noroot = 0;
+    long long last_fit_steps = 0;
+    double last_fit_ms = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch accounting and optional per-launch timing of the path kernel
+    long long launches = 0, path_launches = 0;
+    long long fit_launches = 0, fit_path_launches = 0;
+    double fit_path_ms = 0;
+    int profiling = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    size_t prof_used = 0;
+};
+
+namespace {
+
+bool has_device(int* dev) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return false;
+    return cudaGetDevice(dev) == cudaSuccess;
+}
+
+// Paths per warp unit: a function of the launch shape only (so results do not depend on what
+// else runs): about 16k units, 64..2048 paths each, a multiple of 32.
+int choose_chunk(long long n_items, long long N) {
+    long long target = (n_items * N + 16383) / 16384;
+    long long c = ((target + 31) / 32) * 32;
+    c = std::max(64LL, std::min(2048LL, c));
+    long long nr = ((N + 31) / 32) * 32;
+    c = std::min(c, std::max(32LL, nr));
+    // very long pricing runs: keep the unit count below 2^24
+    while ((N + c - 1) / c > (1LL << 24)) c *= 2;
+    return (int)c;
+}
+
+bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units) {
+    const void* fn = path_fn(o->d, rule, fp64);
+    if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
+    const int nk = a.n_dates - a.m;
+    const size_t real = fp64 ? 8 : 4;
+    size_t smem = nk * real * (1 + (a.uniform ? 0 : 2 * o->d));
+    if (rule != R_NONE) smem += (size_t)(nk - 1) * a.rule_stride * real;
+    smem = (smem + 7) & ~size_t(7);
+    smem += nk * sizeof(int);
+    if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
+    int bps;
+    {
+        std::lock_guard<std::mutex> lk(g_fn_mu);
+        FnInfo& fi = g_fn[fn];
+        if (smem > fi.smem_set) {
+            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+            fi.smem_set = std::max<size_t>(smem, 48 * 1024);
+        }
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
+    }
+    if (bps < 1) bps = 1;
+    long long blocks = (max_units + (kBlock / 32) - 1) / (kBlock / 32);
+    blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
+    void* args[] = {&a};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = o->profiling && !fp64;
+    if (timed) {
+        while (o->prof_ev.size() < o->prof_used + 2) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            o->prof_ev.push_back(e);
+        }
+        e0 = o->prof_ev[o->prof_used];
+        e1 = o->prof_ev[o->prof_used + 1];
+        o->prof_used += 2;
+        CU(cudaEventRecord(e0, o->stream));
+    }
+    CU(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
+    if (timed) CU(cudaEventRecord(e1, o->stream));
+    ++o->launches;
+    ++o->path_launches;
+    return BAP_OK;
+}
+
+// Sum of the recorded path-kernel event pairs (call after the stream is synchronized).
+double prof_collect(bap_option* o) {
+    double tot = 0;
+    for (size_t i = 0; i + 1 < o->prof_used; i += 2) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, o->prof_ev[i], o->prof_ev[i + 1]) == cudaSuccess) tot += ms;
+    }
+    o->prof_used = 0;
+    return tot;
+}
+
+void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
+    memset(&a, 0, sizeof a);
+    a.model = o->dmodel.as<DevModel>();
+    a.m = m;
+    a.mode = mode;
+    a.n_dates = o->n_dates;
+    a.payoff = o->payoff;
+    a.uniform = o->hm.uniform_dates;
+    a.r = o->r;
+    a.K = o->K;
+    const int d = o->d;
+    for (int q = 0; q < d; ++q) {
+        for (int j = 0; j <= q; ++j) {
+            const double l = o->hm.L[q * MAXD + j];
+            const double v = a.uniform ? o->hm.vol2[1][q] * l : l;
+            a.Lf[q * MAXD + j] = (float)v;
+            a.Ld[q * MAXD + j] = v;
+        }
+        a.driftf[q] = (float)o->hm.drift2[1][q];
+        a.driftd[q] = o->hm.drift2[1][q];
+        a.wf[q] = (float)o->hm.w[q];
+    }
+    a.total_steps = o->total_steps.as<unsigned long long>();
+    a.rule_kind = o->rule_kind;
+    a.fitted = o->fitted.as<int>();
+    if (o->rule_kind == R_IZ) {
+        a.rule_src = fp64 ? (const void*)o->coef_d.p : (const void*)o->coef_f.p;
+        a.rule_stride = o->n_bnd * o->n_coef;
+        a.n_bnd = o->n_bnd;
+        a.n_coef = o->n_coef;
+        a.degree = o->degree;
+    } else if (o->rule_kind == R_CMC) {
+        a.rule_src = fp64 ? (const void*)o->rec_d.p : (const void*)o->rec_f.p;
+        a.rule_stride = o->rec_len;
+    }
+}
+
+bap_status set_rule_iz(bap_option* o, int degree) {
+    const int s = o->d - 1;
+    if (s == 0) degree = 0;
+    o->rule_kind = R_IZ;
+    o->n_bnd = (o->payoff == BAP_MAX_CALL && o->d > 1) ? o->d : 1;
+    o->degree = degree;
+    o->n_coef = n_basis(s, degree);
+    const size_t nc = (size_t)(o->n_dates + 1) * o->n_bnd * o->n_coef;
+    TRY(o->coef64.reserve(nc * 8));
+    TRY(o->coef_f.reserve(nc * 4));
+    TRY(o->coef_d.reserve(nc * 8));
+    CU(cudaMemsetAsync(o->coef64.p, 0, nc * 8, o->stream));
+    CU(cudaMemsetAsync(o->coef_f.p, 0, nc * 4, o->stream));
+    CU(cudaMemsetAsync(o->coef_d.p, 0, nc * 8, o->stream));
+    CU(cudaMemsetAsync(o->fitted.p, 0, (o->n_dates + 1) * sizeof(int), o->stream));
+    return BAP_OK;
+}
+
+bap_status set_rule_cmc(bap_option* o, int max_stumps) {
+    o->rule_kind = R_CMC;
+    o->max_stumps = max_stumps;
+    o->rec_len = cmc_record_len(o->d + 1, max_stumps);
+    const size_t nd = o->n_dates + 1;
+    TRY(o->n_stumps.reserve(nd * 4));
+    TRY(o->feat.reserve(nd * max_stumps * 4));
+    TRY(o->thr.reserve(nd * max_stumps * 8));
+    TRY(o->pol.reserve(nd * max_stumps * 4));
+    TRY(o->alpha.reserve(nd * max_stumps * 8));
+    TRY(o->rec_f.reserve(nd * o->rec_len * 4));
+    TRY(o->rec_d.reserve(nd * o->rec_len * 8));
+    CU(cudaMemsetAsync(o->n_stumps.p, 0, nd * 4, o->stream));
+    CU(cudaMemsetAsync(o->feat.p, 0, nd * max_stumps * 4, o->stream));
+    CU(cudaMemsetAsync(o->thr.p, 0, nd * max_stumps * 8, o->stream));
+    CU(cudaMemsetAsync(o->pol.p, 0, nd * max_stumps * 4, o->stream));
+    CU(cudaMemsetAsync(o->alpha.p, 0, nd * max_stumps * 8, o->stream));
+    CU(cudaMemsetAsync(o->rec_f.p, 0, nd * o->rec_len * 4, o->stream));
+    CU(cudaMemsetAsync(o->rec_d.p, 0, nd * o->rec_len * 8, o->stream));
+    CU(cudaMemsetAsync(o->fitted.p, 0, nd * sizeof(int), o->stream));
+    return BAP_OK;
+}
+
+// Scratch for n items of N paths each.
+bap_status reserve_items(bap_option* o, int n, long long N, int C, int max_iter) {
+    const int d = o->d;
+    TRY(o->start.reserve((size_t)n * d * 8));
+    TRY(o->state.reserve((size_t)n * sizeof(ItemState)));
+    TRY(o->pivot.reserve((size_t)n * 4));
+    TRY(o->ctr_item.reserve((size_t)n * 4));
+    TRY(o->active0.reserve((size_t)n * 4));
+    TRY(o->active1.reserve((size_t)n * 4));
+    TRY(o->counts.reserve((size_t)(max_iter + 2) * 4));
+    TRY(o->work.reserve((size_t)(max_iter + 2) * 8));
+    TRY(o->partial.reserve((size_t)n * C * 3 * 8));
+    TRY(o->partial_steps.reserve((size_t)n * C * 8));
+    TRY(o->done.reserve((size_t)n * 4));
+    TRY(o->out_sums.reserve((size_t)n * 3 * 8));
+    TRY(o->out_steps.reserve((size_t)n * 8));
+    TRY(o->label_y.reserve((size_t)n * 8));
+    TRY(o->label.reserve((size_t)n * 4));
+    (void)N;
+    return BAP_OK;
+}
+
+__global__ void iota_kernel(int* p, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = i;
+}
+
+bap_status record_diag(bap_option* o, int m, bool iz) {
+    const int n = o->n_items;
+    const int g = (n + 255) / 256;
+    if (iz) {
+        collect_points_kernel<<<g, 256, 0, o->stream>>>(
+            o->state.as<ItemState>(), n, o->diag_x.as<double>() + (size_t)m * n,
+            o->diag_it.as<int>() + (size_t)m * n, o->diag_st.as<int>() + (size_t)m * n,
+            o->stat_counts.as<int>());
+        ++o->launches;
+    } else {
+        collect_labels_kernel<<<g, 256, 0, o->stream>>>(
+            o->label_y.as<double>(), n, o->diag_x.as<double>() + (size_t)m * n,
+            o->diag_it.as<int>() + (size_t)m * n, o->diag_st.as<int>() + (size_t)m * n);
+        ++o->launches;
+    }
+    CU(cudaGetLastError());
+    return BAP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+
+extern "C" {
+
+const char* bap_last_error(void) { return g_err.c_str(); }
+
+const char* bap_version(void) { return "bap-gb300 1.0 (sm_103a)"; }
+
+bap_status bap_create(const bap_model* md, bap_option** out) {
+    g_err.clear();
+    if (!md || !out) return fail(BAP_EINVAL, "null argument");
+    *out = nullptr;
+    const int d = md->d;
+    if (d < 1 || d > BAP_MAX_D) return fail(BAP_EINVAL, "d=%d outside 1..%d", d, BAP_MAX_D);
+    if (!md->S0 || !md->sigma || !md->delta || !md->rho) return fail(BAP_EINVAL, "null model array");
+    if (!(md->K > 0) || !(md->T > 0)) return fail(BAP_EINVAL, "K and T must be positive");
+    if (md->n_dates < 1 || md->n_dates > BAP_MAX_DATES)
+        return fail(BAP_EINVAL, "n_dates=%d outside 1..%d", md->n_dates, BAP_MAX_DATES);
+    if (md->payoff < BAP_MAX_CALL || md->payoff > BAP_GEO_CALL) return fail(BAP_EINVAL, "bad payoff");
+    if (!std::isfinite(md->r)) return fail(BAP_EINVAL, "bad rate");
+    for (int q = 0; q < d; ++q) {
+        if (!(md->S0[q] > 0) || !std::isfinite(md->S0[q])) return fail(BAP_EINVAL, "S0[%d] must be positive", q);
+        if (!(md->sigma[q] > 0) || !std::isfinite(md->sigma[q])) return fail(BAP_EINVAL, "sigma[%d] must be positive", q);
+        if (!std::isfinite(md->delta[q])) return fail(BAP_EINVAL, "bad delta[%d]", q);
+        if (md->weights && !(md->weights[q] > 0)) return fail(BAP_EINVAL, "weights must be positive");
+        for (int j = 0; j < d; ++j) {
+            const double v = md->rho[q * d + j];
+            if (!std::isfinite(v) || std::fabs(v - md->rho[j * d + q]) > 1e-12 || std::fabs(v) > 1.0 + 1e-12)
+                return fail(BAP_EINVAL, "rho must be a symmetric correlation matrix");
+        }
+        if (std::fabs(md->rho[q * d + q] - 1.0) > 1e-12) return fail(BAP_EINVAL, "rho must have a unit diagonal");
+    }
+    DevModel hm{};
+    hm.d = d;
+    hm.n_dates = md->n_dates;
+    hm.payoff = md->payoff;
+    hm.r = md->r;
+    hm.K = md->K;
+    for (int q = 0; q < d; ++q) {
+        hm.S0[q] = md->S0[q];
+        hm.sigma[q] = md->sigma[q];
+        hm.delta[q] = md->delta[q];
+        hm.w[q] = md->weights ? md->weights[q] : 1.0 / d;
+    }
+    hm.t[0] = 0.0;
+    for (int k = 1; k <= md->n_dates; ++k) {
+        hm.t[k] = md->dates ? md->dates[k - 1] : md->T * k / md->n_dates;
+        if (!(hm.t[k] > hm.t[k - 1])) return fail(BAP_EINVAL, "dates must increase from 0");
+    }
+    if (std::fabs(hm.t[md->n_dates] - md->T) > 1e-12 * md->T) return fail(BAP_EINVAL, "last date must equal T");
+    hm.t[md->n_dates] = md->T;
+
+    int dev;
+    if (!has_device(&dev)) return fail(BAP_ECUDA, "no CUDA device");
+    bap_option* o = new (std::nothrow) bap_option();
+    if (!o) return fail(BAP_ENOMEM, "host allocation");
+    o->device = dev;
+    o->d = d;
+    o->n_dates = md->n_dates;
+    o->payoff = md->payoff;
+    o->r = md->r;
+    o->K = md->K;
+    o->T = md->T;
+    auto cleanup = [&](bap_status s) { bap_destroy(o); return s; };
+    cudaError_t e = cudaDeviceGetAttribute(&o->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
+    e = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
+    o->stream = o->own_stream;
+    if (cudaEventCreate(&o->ev0) != cudaSuccess || cudaEventCreate(&o->ev1) != cudaSuccess)
+        return cleanup(fail(BAP_ECUDA, "event create"));
+    bap_status st;
+    if ((st = o->dmodel.reserve(sizeof(DevModel))) != BAP_OK) return cleanup(st);
+    if ((st = o->fitted.reserve((md->n_dates + 1) * sizeof(int))) != BAP_OK) return cleanup(st);
+    if ((st = o->total_steps.reserve(8)) != BAP_OK) return cleanup(st);
+    if ((st = o->stat_counts.reserve(16)) != BAP_OK) return cleanup(st);
+    if ((st = o->one.reserve(8)) != BAP_OK) return cleanup(st);
+    DevBuf drho;
+    if ((st = drho.reserve((size_t)d * d * 8)) != BAP_OK) return cleanup(st);
+    DevBuf dstatus;
+    if ((st = dstatus.reserve(4)) != BAP_OK) return cleanup(st);
+    e = cudaMemcpyAsync(o->dmodel.p, &hm, sizeof hm, cudaMemcpyHostToDevice, o->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(drho.p, md->rho, (size_t)d * d * 8, cudaMemcpyHostToDevice, o->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o->fitted.p, 0, (md->n_dates + 1) * sizeof(int), o->stream);
+    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
+    model_setup_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), drho.as<double>(), dstatus.as<int>());
+    ++o->launches;
+    int status = -1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&o->hm, o->dmodel.p, sizeof(DevModel), cudaMemcpyDeviceToHost, o->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, dstatus.p, 4, cudaMemcpyDeviceToHost, o->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(o->stream);
+    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
+    if (status != 0) return cleanup(fail(BAP_EINVAL, "rho is not positive definite"));
+    *out = o;
+    return BAP_OK;
+}
+
+bap_status bap_set_stream(bap_option* o, void* s) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    o->stream = reinterpret_cast<cudaStream_t>(s);
+    return BAP_OK;
+}
+
+bap_status bap_set_profiling(bap_option* o, int on) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    o->profiling = on ? 1 : 0;
+    o->prof_used = 0;
+    return BAP_OK;
+}
+
+void bap_destroy(bap_option* o) {
+    if (!o) return;
+    if (o->stream) cudaStreamSynchronize(o->stream);
+    for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
+    if (o->ev0) cudaEventDestroy(o->ev0);
+    if (o->ev1) cudaEventDestroy(o->ev1);
+    if (o->own_stream) cudaStreamDestroy(o->own_stream);
+    delete o;
+}
+
+bap_status bap_fit_boundary(bap_option* o, const bap_iz_params* p) {
+    g_err.clear();
+    if (!o || !p) return fail(BAP_EINVAL, "null argument");
+    if (p->J < 1 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 1..8192", p->J);
+    if (p->N1 < 1 || p->N1 > (1LL << 31)) return fail(BAP_EINVAL, "N1 outside 1..2^31");
+    if (p->max_iter < 1 || p->max_iter > 200) return fail(BAP_EINVAL, "max_iter outside 1..200");
+    if (p->degree < 0 || p->degree > 2) return fail(BAP_EINVAL, "degree outside 0..2");
+    if (!(p->f_tol >= 0) || !(p->x_tol >= 0)) return fail(BAP_EINVAL, "negative tolerance");
+    if (p->fixed_point && !(p->fp_eps > 0)) return fail(BAP_EINVAL, "fp_eps must be positive");
+    if (o->n_dates < 2) {
+        TRY(set_rule_iz(o, p->degree));
+        o->method = 0;
+        o->n_items = 0;
+        o->last_fit_steps = 0;
+        o->last_noconv = o->last_noroot = 0;
+        return BAP_OK;
+    }
+    const int d = o->d, s = d - 1;
+    o->launches = o->path_launches = 0;
+    o->prof_used = 0;
+    TRY(set_rule_iz(o, p->degree));
+    const int J = p->J;
+    const int n = o->n_bnd * J;
+    o->n_items = n;
+    const int chunk = choose_chunk(n, p->N1);
+    const int C = (int)((p->N1 + chunk - 1) / chunk);
+    TRY(reserve_items(o, n, p->N1, C, p->max_iter));
+    TRY(o->korobov_a.reserve(8));
+    TRY(o->merit.reserve((size_t)(J + 1) * 8));
+    TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
+    TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
+    TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
+    cudaStream_t st = o->stream;
+    CU(cudaMemsetAsync(o->diag_x.p, 0, (size_t)(o->n_dates + 1) * n * 8, st));
+    CU(cudaMemsetAsync(o->diag_it.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->diag_st.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
+    iota_kernel<<<(n + 255) / 256, 256, 0, st>>>(o->ctr_item.as<int>(), n);
+    ++o->launches;
+    CU(cudaEventRecord(o->ev0, st));
+    // [glp]
+    if (s >= 2 && J > 2) {
+        const int warps = J - 1;
+        korobov_merit_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(J, s, o->merit.as<double>());
+        ++o->launches;
+    }
+    korobov_pick_kernel<<<1, 256, 0, st>>>(J, s, o->merit.as<double>(), o->korobov_a.as<int>());
+    ++o->launches;
+    CU(cudaGetLastError());
+    const RoundKeys rk0 = make_round_keys(p->seed, P_IZ, 0);
+    (void)rk0;
+    for (int m = o->n_dates - 1; m >= 1; --m) {
+        CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
+        CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
+        iz_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(
+            o->dmodel.as<DevModel>(), m, J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
+            o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), o->counts.as<int>());
+        ++o->launches;
+        CU(cudaGetLastError());
+        for (int it = 0; it < p->max_iter; ++it) {
+            PathArgs a;
+            base_args(o, a, m, MODE_NEWTON, false);
+            a.rk = make_round_keys(p->seed, P_IZ, (uint32_t)m);
+            a.N = p->N1;
+            a.chunk = chunk;
+            a.C = C;
+            a.active = (it & 1) ? o->active1.as<int>() : o->active0.as<int>();
+            a.n_active = o->counts.as<int>() + it;
+            a.work = o->work.as<unsigned long long>() + it;
+            a.start = o->start.as<double>();
+            a.ctr_item = o->ctr_item.as<int>();
+            a.pivot = o->pivot.as<int>();
+            a.partial = o->partial.as<double>();
+            a.partial_steps = o->partial_steps.as<long long>();
+            a.done = o->done.as<int>();
+            a.state = o->state.as<ItemState>();
+            a.next_active = (it & 1) ? o->active0.as<int>() : o->active1.as<int>();
+            a.next_count = o->counts.as<int>() + it + 1;
+            a.f_tol = p->f_tol;
+            a.x_tol = p->x_tol;
+            a.fp_eps = p->fp_eps;
+            a.max_iter = p->max_iter;
+            a.fixed_point = p->fixed_point;
+            TRY(launch_path(o, a, R_IZ, false, (long long)n * C));
+        }
+        ls_fit_kernel<<<o->n_bnd, 256, 0, st>>>(
+            o->dmodel.as<DevModel>(), m, J, o->n_bnd, o->degree, o->n_coef, o->start.as<double>(),
+            o->state.as<ItemState>(), o->coef64.as<double>(), o->coef_f.as<float>(),
+            o->coef_d.as<double>(), o->fitted.as<int>());
+        ++o->launches;
+        CU(cudaGetLastError());
+        TRY(record_diag(o, m, true));
+    }
+    CU(cudaEventRecord(o->ev1, st));
+    unsigned long long steps = 0;
+    int counts[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(&steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(counts, o->stat_counts.p, 16, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, o->ev0, o->ev1));
+    o->last_fit_ms = ms;
+    o->last_fit_steps = (long long)steps;
+    o->last_noconv = counts[0];
+    o->last_noroot = counts[1];
+    o->method = 0;
+    o->fit_launches = o->launches;
+    o->fit_path_launches = o->path_launches;
+    o->fit_path_ms = prof_collect(o);
+    return counts[0] > 0 ? BAP_ENOCONV : BAP_OK;
+}
+
+bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
+    g_err.clear();
+    if (!o || !p) return fail(BAP_EINVAL, "null argument");
+    if (p->J < 2 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 2..8192", p->J);
+    if (p->N2 < 1 || p->N2 > (1LL << 31)) return fail(BAP_EINVAL, "N2 outside 1..2^31");
+    if (p->n_stumps < 1 || p->n_stumps > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "n_stumps outside 1..%d", BAP_MAX_STUMPS);
+    o->launches = o->path_launches = 0;
+    o->prof_used = 0;
+    TRY(set_rule_cmc(o, p->n_stumps));
+    o->method = 1;
+    if (o->n_dates < 2) {
+        o->n_items = 0;
+        o->last_fit_steps = 0;
+        return BAP_OK;
+    }
+    const int J = p->J;
+    const int n = J;
+    o->n_items = n;
+    const int chunk = choose_chunk(n, p->N2);
+    const int C = (int)((p->N2 + chunk - 1) / chunk);
+    const int d = o->d, nF = d + 1;
+    TRY(reserve_items(o, n, p->N2, C, 1));
+    TRY(o->sorted_v.reserve((size_t)nF * J * 8));
+    TRY(o->sorted_i.reserve((size_t)nF * J * 4));
+    TRY(o->err.reserve((size_t)nF * J * 8));
+    TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
+    TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
+    TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
+    cudaStream_t st = o->stream;
+    CU(cudaMemsetAsync(o->diag_x.p, 0, (size_t)(o->n_dates + 1) * n * 8, st));
+    CU(cudaMemsetAsync(o->diag_it.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->diag_st.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    const size_t ab_smem = (size_t)J * 8 + (size_t)P2 * 12;
+    CU(cudaFuncSetAttribute(adaboost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(ab_smem, 48 * 1024)));
+    CU(cudaEventRecord(o->ev0, st));
+    for (int m = o->n_dates - 1; m >= 1; --m) {
+        train_points_kernel<<<(J + 127) / 128, 128, 0, st>>>(
+            o->dmodel.as<DevModel>(), m, make_round_keys(p->seed, P_TRAIN, (uint32_t)m), J,
+            o->start.as<double>(), o->ctr_item.as<int>());
+        ++o->launches;
+        CU(cudaGetLastError());
+        CU(cudaMemsetAsync(o->work.p, 0, 8, st));
+        set_int_kernel<<<1, 32, 0, st>>>(o->counts.as<int>(), J);
+        ++o->launches;
+        PathArgs a;
+        base_args(o, a, m, MODE_LABEL, false);
+        a.rk = make_round_keys(p->seed, P_CMC, (uint32_t)m);
+        a.N = p->N2;
+        a.chunk = chunk;
+        a.C = C;
+        a.active = nullptr;
+        a.n_active = o->counts.as<int>();
+        a.work = o->work.as<unsigned long long>();
+        a.start = o->start.as<double>();
+        a.ctr_item = o->ctr_item.as<int>();
+        a.pivot = nullptr;
+        a.partial = o->partial.as<double>();
+        a.partial_steps = o->partial_steps.as<long long>();
+        a.done = o->done.as<int>();
+        a.label_y = o->label_y.as<double>();
+        a.label = o->label.as<int>();
+        TRY(launch_path(o, a, R_CMC, false, (long long)n * C));
+        adaboost_kernel<<<1, 1024, ab_smem, st>>>(
+            o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label_y.as<double>(),
+            o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(),
+            o->err.as<double>(), o->max_stumps, o->n_stumps.as<int>(), o->feat.as<int>(),
+            o->thr.as<double>(), o->pol.as<int>(), o->alpha.as<double>(), o->rec_len,
+            o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
+        ++o->launches;
+        CU(cudaGetLastError());
+        TRY(record_diag(o, m, false));
+    }
+    CU(cudaEventRecord(o->ev1, st));
+    unsigned long long steps = 0;
+    CU(cudaMemcpyAsync(&steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, o->ev0, o->ev1));
+    o->last_fit_ms = ms;
+    o->last_fit_steps = (long long)steps;
+    o->last_noconv = o->last_noroot = 0;
+    o->fit_launches = o->launches;
+    o->fit_path_launches = o->path_launches;
+    o->fit_path_ms = prof_collect(o);
+    return BAP_OK;
+}
+
+static bap_status run_sums(bap_option* o, int m, int mode, bool fp64, const RoundKeys& rk, int n_items,
+                           long long N, const int* d_item_ids, const int* d_pivots,
+                           double* d_start, double* h_sums, long long* h_steps, float* ms) {
+    const int chunk = choose_chunk(n_items, N);
+    const int C = (int)((N + chunk - 1) / chunk);
+    TRY(o->partial.reserve((size_t)n_items * C * 3 * 8));
+    TRY(o->partial_steps.reserve((size_t)n_items * C * 8));
+    TRY(o->done.reserve((size_t)n_items * 4));
+    TRY(o->out_sums.reserve((size_t)n_items * 3 * 8));
+    TRY(o->out_steps.reserve((size_t)n_items * 8));
+    TRY(o->work.reserve(16));
+    TRY(o->counts.reserve(16));
+    cudaStream_t st = o->stream;
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n_items * 4, st));
+    CU(cudaMemsetAsync(o->work.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    set_int_kernel<<<1, 32, 0, st>>>(o->counts.as<int>(), n_items);
+    ++o->launches;
+    PathArgs a;
+    base_args(o, a, m, mode, fp64);
+    a.rk = rk;
+    a.N = N;
+    a.chunk = chunk;
+    a.C = C;
+    a.active = nullptr;
+    a.n_active = o->counts.as<int>();
+    a.work = o->work.as<unsigned long long>();
+    a.start = d_start;
+    a.ctr_item = d_item_ids;
+    a.pivot = d_pivots;
+    a.partial = o->partial.as<double>();
+    a.partial_steps = o->partial_steps.as<long long>();
+    a.done = o->done.as<int>();
+    a.out_sums = o->out_sums.as<double>();
+    a.out_steps = o->out_steps.as<long long>();
+    a.trace_tau = o->trace_tau.as<int>();
+    a.trace_phi = o->trace_phi.as<double>();
+    if (ms) CU(cudaEventRecord(o->ev0, st));
+    TRY(launch_path(o, a, o->rule_kind, fp64, (long long)n_items * C));
+    if (ms) CU(cudaEventRecord(o->ev1, st));
+    CU(cudaMemcpyAsync(h_sums, o->out_sums.p, (size_t)n_items * 3 * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(h_steps, o->out_steps.p, (size_t)n_items * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (ms) CU(cudaEventElapsedTime(ms, o->ev0, o->ev1));
+    return BAP_OK;
+}
+
+bap_status bap_price(bap_option* o, int64_t n_paths, uint64_t seed, bap_result* res) {
+    g_err.clear();
+    if (!o || !res) return fail(BAP_EINVAL, "null argument");
+    if (n_paths < 2 || n_paths > (1LL << 40)) return fail(BAP_EINVAL, "n_paths outside 2..2^40");
+    memset(res, 0, sizeof *res);
+    o->launches = o->path_launches = 0;
+    o->prof_used = 0;
+    DevBuf s0;
+    TRY(s0.reserve((size_t)o->d * 8));
+    copy_s0_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), s0.as<double>());
+    ++o->launches;
+    CU(cudaGetLastError());
+    const RoundKeys rk = make_round_keys(seed, P_PRICE, 0);
+    double sums[3], sums64[3];
+    long long steps = 0, steps64 = 0;
+    float ms = 0;
+    TRY(run_sums(o, 0, MODE_SUMS, false, rk, 1, n_paths, nullptr, nullptr, s0.as<double>(), sums, &steps, &ms));
+    TRY(run_sums(o, 0, MODE_SUMS, true, rk, 1, n_paths, nullptr, nullptr, s0.as<double>(), sums64, &steps64, nullptr));
+    const double N = (double)n_paths;
+    const double mean = sums[0] / N;
+    double var = (sums[1] - N * mean * mean) / (N - 1.0);
+    if (var < 0) var = 0;
+    res->price = mean;
+    res->var = var;
+    res->se = std::sqrt(var / N);
+    res->ci95 = 1.96 * res->se;
+    res->n_paths = n_paths;
+    res->path_steps = steps;
+    res->fp64_delta = mean - sums64[0] / N;
+    res->n_noconv = o->last_noconv;
+    res->n_noroot = o->last_noroot;
+    res->fit_path_steps = o->last_fit_steps;
+    res->fit_ms = o->last_fit_ms;
+    res->price_ms = ms;
+    res->kernel_launches = o->fit_launches + o->launches;
+    res->path_launches = o->fit_path_launches + o->path_launches;
+    res->path_kernel_ms = o->fit_path_ms + prof_collect(o);
+    return BAP_OK;
+}
+
+bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t seed, int n_items,
+                                  const int* item_ids, const int* pivots, const double* starts,
+                                  int64_t N, double* sums, int64_t* steps) {
+    g_err.clear();
+    if (!o || !item_ids || !starts || !sums || !steps) return fail(BAP_EINVAL, "null argument");
+    if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
+    if (n_items < 1 || N < 1 || N > (1LL << 31)) return fail(BAP_EINVAL, "bad n_items or N");
+    if (purpose < 1 || purpose > 4) return fail(BAP_EINVAL, "bad purpose");
+    const int d = o->d;
+    for (int i = 0; i < n_items; ++i) {
+        for (int q = 0; q < d; ++q)
+            if (!(starts[(size_t)i * d + q] > 0)) return fail(BAP_EINVAL, "start points must be positive");
+        if (pivots && (pivots[i] < -1 || pivots[i] >= d)) return fail(BAP_EINVAL, "bad pivot");
+    }
+    DevBuf ds, di, dp;
+    TRY(ds.reserve((size_t)n_items * d * 8));
+    TRY(di.reserve((size_t)n_items * 4));
+    if (pivots) TRY(dp.reserve((size_t)n_items * 4));
+    CU(cudaMemcpyAsync(ds.p, starts, (size_t)n_items * d * 8, cudaMemcpyHostToDevice, o->stream));
+    CU(cudaMemcpyAsync(di.p, item_ids, (size_t)n_items * 4, cudaMemcpyHostToDevice, o->stream));
+    if (pivots) CU(cudaMemcpyAsync(dp.p, pivots, (size_t)n_items * 4, cudaMemcpyHostToDevice, o->stream));
+    std::vector<long long> st(n_items);
+    TRY(run_sums(o, m, MODE_SUMS, false, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), n_items, N,
+                 di.as<int>(), pivots ? dp.as<int>() : nullptr, ds.as<double>(), sums, st.data(), nullptr));
+    for (int i = 0; i < n_items; ++i) steps[i] = st[i];
+    return BAP_OK;
+}
+
+bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int item_id,
+                           const double* start, int64_t N, int* tau, double* disc_phi) {
+    g_err.clear();
+    if (!o || !start || !tau || !disc_phi) return fail(BAP_EINVAL, "null argument");
+    if (m < 0 || m >= o->n_dates) return fail(BAP_EINVAL, "bad m");
+    if (N < 1 || N > (1LL << 26)) return fail(BAP_EINVAL, "N outside 1..2^26");
+    const int d = o->d;
+    DevBuf ds, di;
+    TRY(ds.reserve((size_t)d * 8));
+    TRY(di.reserve(4));
+    TRY(o->trace_tau.reserve((size_t)N * 4));
+    TRY(o->trace_phi.reserve((size_t)N * 8));
+    CU(cudaMemcpyAsync(ds.p, start, (size_t)d * 8, cudaMemcpyHostToDevice, o->stream));
+    CU(cudaMemcpyAsync(di.p, &item_id, 4, cudaMemcpyHostToDevice, o->stream));
+    double sums[3];
+    long long steps;
+    TRY(run_sums(o, m, MODE_TRACE, false, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), 1, N,
+                 di.as<int>(), nullptr, ds.as<double>(), sums, &steps, nullptr));
+    CU(cudaMemcpy(tau, o->trace_tau.p, (size_t)N * 4, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(disc_phi, o->trace_phi.p, (size_t)N * 8, cudaMemcpyDeviceToHost));
+    return BAP_OK;
+}
+
+bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_t step, int d,
+                         int64_t count, uint32_t* words, double* z) {
+    g_err.clear();
+    if (d < 1 || d > 16 || count < 1 || count > (1LL << 26)) return fail(BAP_EINVAL, "bad d or count");
+    int dev;
+    if (!has_device(&dev)) return fail(BAP_ECUDA, "no CUDA device");
+    const int nc = (d + 3) / 4;
+    DevBuf dw, dz;
+    if (words) TRY(dw.reserve((size_t)count * nc * 16));
+    if (z) TRY(dz.reserve((size_t)count * d * 8));
+    rng_debug_kernel<<<(unsigned)((count + 255) / 256), 256>>>(
+        make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), w1, step, d, count,
+        words ? dw.as<uint32_t>() : nullptr, z ? dz.as<double>() : nullptr);
+    CU(cudaGetLastError());
+    if (words) CU(cudaMemcpy(words, dw.p, (size_t)count * nc * 16, cudaMemcpyDeviceToHost));
+    if (z) CU(cudaMemcpy(z, dz.p, (size_t)count * d * 8, cudaMemcpyDeviceToHost));
+    return BAP_OK;
+}
+
+bap_status bap_fit_points(const bap_option* o, int m, int* n_items, double* x, int* iters, int* status) {
+    g_err.clear();
+    if (!o || !n_items) return fail(BAP_EINVAL, "null argument");
+    if (o->method < 0) return fail(BAP_ESTATE, "no fit yet");
+    if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "bad m");
+    const int n = o->n_items;
+    const int cap = *n_items;
+    *n_items = n;
+    if (!x && !iters && !status) return BAP_OK;
+    const int k = std::min(cap, n);
+    if (k <= 0) return BAP_OK;
+    CU(cudaStreamSynchronize(o->stream));
+    if (x) CU(cudaMemcpy(x, o->diag_x.as<double>() + (size_t)m * n, (size_t)k * 8, cudaMemcpyDeviceToHost));
+    if (iters) CU(cudaMemcpy(iters, o->diag_it.as<int>() + (size_t)m * n, (size_t)k * 4, cudaMemcpyDeviceToHost));
+    if (status) CU(cudaMemcpy(status, o->diag_st.as<int>() + (size_t)m * n, (size_t)k * 4, cudaMemcpyDeviceToHost));
+    return BAP_OK;
+}
+
+bap_status bap_export_rules(const bap_option* o, double* buf, size_t* len) {
+    g_err.clear();
+    if (!o || !len) return fail(BAP_EINVAL, "null argument");
+    const int nd = o->n_dates + 1;
+    const int kind = o->rule_kind;
+    size_t need = 6 + nd;
+    if (kind == R_IZ) need += (size_t)nd * o->n_bnd * o->n_coef;
+    if (kind == R_CMC) need += (size_t)nd * o->max_stumps * 4 + nd;
+    if (!buf) { *len = need; return BAP_OK; }
+    std::vector<double> out(need, 0.0);
+    out[0] = kind;
+    out[1] = o->n_dates;
+    out[2] = o->n_bnd;
+    out[3] = o->degree;
+    out[4] = o->n_coef;
+    out[5] = o->max_stumps;
+    std::vector<int> fit(nd);
+    CU(cudaStreamSynchronize(o->stream));
+    CU(cudaMemcpy(fit.data(), o->fitted.p, nd * 4, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < nd; ++k) out[6 + k] = fit[k];
+    size_t off = 6 + nd;
+    if (kind == R_IZ) {
+        CU(cudaMemcpy(out.data() + off, o->coef64.p, (size_t)nd * o->n_bnd * o->n_coef * 8, cudaMemcpyDeviceToHost));
+    } else if (kind == R_CMC) {
+        const size_t ns = (size_t)nd * o->max_stumps;
+        std::vector<int> f(ns), pl(ns), nst(nd);
+        std::vector<double> th(ns), al(ns);
+        CU(cudaMemcpy(f.data(), o->feat.p, ns * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(pl.data(), o->pol.p, ns * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(th.data(), o->thr.p, ns * 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(al.data(), o->alpha.p, ns * 8, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(nst.data(), o->n_stumps.p, nd * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < ns; ++i) {
+            out[off + 4 * i + 0] = f[i];
+            out[off + 4 * i + 1] = th[i];
+            out[off + 4 * i + 2] = pl[i];
+            out[off + 4 * i + 3] = al[i];
+        }
+        for (int k = 0; k < nd; ++k) out[off + 4 * ns + k] = nst[k];
+    }
+    memcpy(buf, out.data(), std::min(*len, need) * 8);
+    *len = need;
+    return BAP_OK;
+}
+
+bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
+    g_err.clear();
+    if (!o || !buf || len < 6) return fail(BAP_EINVAL, "null or short buffer");
+    const int kind = (int)buf[0];
+    const int nd = o->n_dates + 1;
+    if ((int)buf[1] != o->n_dates) return fail(BAP_EINVAL, "n_dates mismatch");
+    if (len < (size_t)(6 + nd)) return fail(BAP_EINVAL, "short buffer");
+    std::vector<int> fit(nd);
+    for (int k = 0; k < nd; ++k) fit[k] = buf[6 + k] != 0.0;
+    const size_t off = 6 + nd;
+    if (kind == R_NONE) {
+        o->rule_kind = R_NONE;
+        CU(cudaMemsetAsync(o->fitted.p, 0, nd * 4, o->stream));
+        CU(cudaStreamSynchronize(o->stream));
+        return BAP_OK;
+    }
+    if (kind == R_IZ) {
+        const int degree = (int)buf[3];
+        if (degree < 0 || degree > 2) return fail(BAP_EINVAL, "bad degree");
+        TRY(set_rule_iz(o, degree));
+        if ((int)buf[2] != o->n_bnd || (int)buf[4] != o->n_coef) return fail(BAP_EINVAL, "boundary shape mismatch");
+        const size_t nc = (size_t)nd * o->n_bnd * o->n_coef;
+        if (len < off + nc) return fail(BAP_EINVAL, "short buffer");
+        CU(cudaMemcpyAsync(o->coef64.p, buf + off, nc * 8, cudaMemcpyHostToDevice, o->stream));
+        stage_iz_kernel<<<(nd * o->n_bnd + 127) / 128, 128, 0, o->stream>>>(
+            o->coef64.as<double>(), o->n_dates, o->n_bnd, o->n_coef, o->d - 1, o->degree, o->K,
+            o->coef_f.as<float>(), o->coef_d.as<double>());
+        ++o->launches;
+        CU(cudaGetLastError());
+    } else if (kind == R_CMC) {
+        const int ms = (int)buf[5];
+        if (ms < 1 || ms > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "bad max_stumps");
+        TRY(set_rule_cmc(o, ms));
+        const size_t ns = (size_t)nd * ms;
+        if (len < off + 4 * ns + nd) return fail(BAP_EINVAL, "short buffer");
+        std::vector<int> f(ns), pl(ns), nst(nd);
+        std::vector<double> th(ns), al(ns);
+        for (size_t i = 0; i < ns; ++i) {
+            f[i] = (int)buf[off + 4 * i];
+            th[i] = buf[off + 4 * i + 1];
+            pl[i] = (int)buf[off + 4 * i + 2];
+            al[i] = buf[off + 4 * i + 3];
+            if (f[i] < 0 || f[i] > o->d || (pl[i] != 1 && pl[i] != -1 && al[i] != 0.0))
+                return fail(BAP_EINVAL, "bad stump");
+        }
+        for (int k = 0; k < nd; ++k) {
+            nst[k] = (int)buf[off + 4 * ns + k];
+            if (nst[k] < 0 || nst[k] > ms) return fail(BAP_EINVAL, "bad stump count");
+        }
+        CU(cudaMemcpyAsync(o->feat.p, f.data(), ns * 4, cudaMemcpyHostToDevice, o->stream));
+        CU(cudaMemcpyAsync(o->pol.p, pl.data(), ns * 4, cudaMemcpyHostToDevice, o->stream));
+        CU(cudaMemcpyAsync(o->thr.p, th.data(), ns * 8, cudaMemcpyHostToDevice, o->stream));
+        CU(cudaMemcpyAsync(o->alpha.p, al.data(), ns * 8, cudaMemcpyHostToDevice, o->stream));
+        CU(cudaMemcpyAsync(o->n_stumps.p, nst.data(), nd * 4, cudaMemcpyHostToDevice, o->stream));
+        stage_cmc_kernel<<<(nd + 31) / 32, 32, 0, o->stream>>>(
+            o->n_dates, o->d + 1, ms, o->n_stumps.as<int>(), o->feat.as<int>(), o->thr.as<double>(),
+            o->pol.as<int>(), o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(), o->rec_d.as<double>());
+        ++o->launches;
+        CU(cudaGetLastError());
+    } else {
+        return fail(BAP_EINVAL, "bad rule kind %d", kind);
+    }
+    CU(cudaMemcpyAsync(o->fitted.p, fit.data(), nd * 4, cudaMemcpyHostToDevice, o->stream));
+    CU(cudaStreamSynchronize(o->stream));
+    return BAP_OK;
+}
+
+}  // extern "C"

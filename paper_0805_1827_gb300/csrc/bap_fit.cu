@@ -1,0 +1,771 @@
+// bap_fit.cu -- device kernels around the path kernel: model set-up, the Korobov lattice
+// ([glp]), boundary-point set-up, the FP64 least-squares boundary fit ([reg]), CMC training
+// points and device AdaBoost ([class]), and the staging of fitted rules for the path kernel.
+#include "bap_fit.cuh"
+
+#include <cfloat>
+
+namespace bap {
+
+// ---------------------------------------------------------------------------------------------
+// Model set-up: FP64 Cholesky factor of rho and the per-date stepping constants (log2 units).
+// status: 0 ok, 1 rho not positive definite.
+
+__global__ void model_setup_kernel(DevModel* M, const double* rho, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int d = M->d;
+    for (int i = 0; i < MAXD * MAXD; ++i) M->L[i] = 0.0;
+    int ok = 1;
+    for (int j = 0; j < d && ok; ++j) {
+        double s = rho[j * d + j];
+        for (int k = 0; k < j; ++k) s -= M->L[j * MAXD + k] * M->L[j * MAXD + k];
+        if (!(s > 1e-14)) { ok = 0; break; }
+        const double ljj = sqrt(s);
+        M->L[j * MAXD + j] = ljj;
+        for (int i = j + 1; i < d; ++i) {
+            double v = rho[i * d + j];
+            for (int k = 0; k < j; ++k) v -= M->L[i * MAXD + k] * M->L[j * MAXD + k];
+            M->L[i * MAXD + j] = v / ljj;
+        }
+    }
+    const double inv_ln2 = 1.4426950408889634;
+    int uniform = 1;
+    const double dt1 = M->t[1] - M->t[0];
+    for (int k = 1; k <= M->n_dates; ++k) {
+        const double dt = M->t[k] - M->t[k - 1];
+        if (fabs(dt - dt1) > 1e-12 * M->t[M->n_dates]) uniform = 0;
+        for (int q = 0; q < d; ++q) {
+            M->drift2[k][q] = (M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q]) * dt * inv_ln2;
+            M->vol2[k][q] = M->sigma[q] * sqrt(dt) * inv_ln2;
+        }
+    }
+    M->uniform_dates = uniform;
+    *status = ok ? 0 : 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// [glp] Korobov rank-1 lattice (Section 2.3): the multiplier a minimising the P_2 figure of
+// merit -1 + (1/J) sum_j prod_k (1 + 2 pi^2 B_2({j a^k / J})), B_2(x) = x^2 - x + 1/6, over
+// a in [1, J) coprime to J; ties within 1e-9 (relative) go to the smallest a.
+
+__device__ inline unsigned gcd_u(unsigned a, unsigned b) {
+    while (b) { unsigned t = a % b; a = b; b = t; }
+    return a;
+}
+
+__global__ void korobov_merit_kernel(int J, int s, double* merit) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int a = warp + 1;
+    if (a >= J) return;
+    if (gcd_u((unsigned)a, (unsigned)J) != 1u) {
+        if (lane == 0) merit[a] = INFINITY;
+        return;
+    }
+    unsigned long long g[MAXD];
+    g[0] = 1;
+    for (int k = 1; k < s; ++k) g[k] = (g[k - 1] * (unsigned long long)a) % (unsigned long long)J;
+    const double c2 = 2.0 * 9.869604401089358;   // 2 pi^2
+    double sum = 0.0;
+    for (int j = lane; j < J; j += 32) {
+        double prod = 1.0;
+        for (int k = 0; k < s; ++k) {
+            const double u = (double)(((unsigned long long)j * g[k]) % (unsigned long long)J) / (double)J;
+            prod *= 1.0 + c2 * (u * u - u + 1.0 / 6.0);
+        }
+        sum += prod;
+    }
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+    if (lane == 0) merit[a] = -1.0 + sum / (double)J;
+}
+
+__global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_a) {
+    __shared__ double smin[32];
+    __shared__ int sidx[32];
+    if (s <= 1 || J <= 2) {
+        if (threadIdx.x == 0) *out_a = 1;
+        return;
+    }
+    double mn = INFINITY;
+    for (int a = 1 + threadIdx.x; a < J; a += blockDim.x) mn = fmin(mn, merit[a]);
+    for (int off = 16; off > 0; off >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, off));
+    if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < blockDim.x / 32 ? smin[threadIdx.x] : INFINITY;
+        for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, off));
+        if (threadIdx.x == 0) smin[0] = v;
+    }
+    __syncthreads();
+    const double vmin = smin[0];
+    const double tol = 1e-9 * fmax(fabs(vmin), 1e-300);
+    int best = J;
+    for (int a = 1 + threadIdx.x; a < J; a += blockDim.x)
+        if (merit[a] <= vmin + tol && a < best) best = a;
+    for (int off = 16; off > 0; off >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, off));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sidx[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = J;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) b = min(b, sidx[w]);
+        *out_a = b < J ? b : 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// I&Z items of date m (item = b*J + j): the other assets at the lognormal quantiles of the
+// shifted lattice point frac(j g / J + 1/(2J)), the pivot at the Newton start, and the bracket.
+
+__global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
+                                double* start, ItemState* state, int* pivot, int* active,
+                                int* count) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= n_bnd * J) return;
+    const int d = M->d, s = d - 1;
+    const int b = item / J, j = item - b * J;
+    const int p = n_bnd > 1 ? b : 0;
+    const double tm = M->t[m];
+    const double K = M->K;
+    double* S = start + (size_t)item * d;
+    unsigned long long g = 1;
+    const unsigned long long a = (unsigned long long)(*korobov_a);
+    int c = 0;
+    for (int q = 0; q < d; ++q) {
+        if (q == p) continue;
+        const double u = ((double)(((unsigned long long)j * g) % (unsigned long long)J) + 0.5) / (double)J;
+        const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+        S[q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * normcdfinv(u));
+        g = (g * a) % (unsigned long long)J;
+        ++c;
+    }
+    (void)s;
+    ItemState st;
+    st.iters = 0;
+    st.status = ST_OK;
+    st.done = 0;
+    st.pivot = p;
+    st.dx_old = INFINITY;
+    st.dx = INFINITY;
+    bool live = true;
+    if (M->payoff == BAP_MAX_CALL) {
+        double mx = K;
+        for (int q = 0; q < d; ++q)
+            if (q != p && S[q] > mx) mx = S[q];
+        st.lo = mx;
+        st.hi = INFINITY;
+        st.x = mx * (1.0 + 1e-3);
+    } else if (M->payoff == BAP_GEO_CALL) {
+        double lg = log(K);
+        for (int q = 0; q < d; ++q)
+            if (q != p) lg -= M->w[q] * log(S[q]);
+        st.lo = exp(lg / M->w[p]);
+        st.hi = INFINITY;
+        st.x = st.lo * (1.0 + 1e-3);
+    } else {
+        double top = K;
+        for (int q = 0; q < d; ++q)
+            if (q != p) top -= M->w[q] * S[q];
+        top /= M->w[p];
+        if (!(top > 0)) {
+            st.x = 0.0;
+            st.lo = 0.0;
+            st.hi = 0.0;
+            st.status = ST_NOROOT;
+            st.done = 1;
+            live = false;
+        } else {
+            st.lo = 0.0;
+            st.hi = top;
+            st.x = top * (1.0 - 1e-3);
+        }
+    }
+    S[p] = st.x;
+    state[item] = st;
+    pivot[item] = p;
+    if (live) {
+        const int pos = atomicAdd(count, 1);
+        active[pos] = item;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Staging of an I&Z boundary (date m, boundary b) for the path kernel: coefficients of
+// x/K = B(y/K) in [1, y_a, y_a y_b (a<=b)] order become the Horner layout
+// [K c_0, for a: c_a, c_ab / K (b = a..s-1)] of B''(S) = K B(S/K) in price units.
+
+__device__ void stage_iz_one(const double* c, int s, int degree, double K, float* out_f,
+                             double* out_d) {
+    out_f[0] = (float)(K * c[0]);
+    out_d[0] = K * c[0];
+    if (degree == 1) {
+        for (int t = 0; t < s; ++t) {
+            out_f[1 + t] = (float)c[1 + t];
+            out_d[1 + t] = c[1 + t];
+        }
+    } else if (degree == 2) {
+        int o = 1, qidx = 1 + s;
+        for (int t = 0; t < s; ++t) {
+            out_f[o] = (float)c[1 + t];
+            out_d[o] = c[1 + t];
+            ++o;
+            for (int u = t; u < s; ++u, ++qidx, ++o) {
+                out_f[o] = (float)(c[qidx] / K);
+                out_d[o] = c[qidx] / K;
+            }
+        }
+    }
+}
+
+__global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
+                                int degree, double K, float* coef_f, double* coef_d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (n_dates + 1) * n_bnd) return;
+    const size_t o = (size_t)i * n_coef;
+    stage_iz_one(coef64 + o, s, degree, K, coef_f + o, coef_d + o);
+}
+
+// ---------------------------------------------------------------------------------------------
+// [reg] Least squares of x/K on the polynomial basis of y/K for boundary b of date m (FP64).
+// Points with status "no root" are left out; fewer points than coefficients -> degree 0 (their
+// mean); no points -> "never exercise".  Normal equations on the diagonally equilibrated Gram
+// matrix, solved by Cholesky; a Cholesky failure also falls back to the mean.
+
+__device__ inline double basis_val(const double* y, int bi, int bj) {
+    const double a = bi < 0 ? 1.0 : y[bi];
+    const double b = bj < 0 ? 1.0 : y[bj];
+    return a * b;
+}
+
+__global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
+                              const double* start, const ItemState* state, double* coef64,
+                              float* coef_f, double* coef_d, int* fitted) {
+    const int b = blockIdx.x;
+    const int d = M->d, s = d - 1;
+    const int p = n_bnd > 1 ? b : 0;
+    const double K = M->K;
+    __shared__ int bi[MAXCOEF], bj[MAXCOEF];
+    __shared__ double G[MAXCOEF * MAXCOEF];
+    __shared__ double rhs[MAXCOEF];
+    __shared__ double red[32];
+    __shared__ int red_n[32];
+    __shared__ double coef[MAXCOEF];
+    const int P = n_coef;
+    if (threadIdx.x == 0) {
+        int o = 0;
+        bi[o] = -1; bj[o] = -1; ++o;
+        if (degree >= 1)
+            for (int t = 0; t < s; ++t) { bi[o] = t; bj[o] = -1; ++o; }
+        if (degree >= 2)
+            for (int t = 0; t < s; ++t)
+                for (int u = t; u < s; ++u) { bi[o] = t; bj[o] = u; ++o; }
+    }
+    __syncthreads();
+    // count of used points and their mean
+    double sx = 0.0;
+    int nu = 0;
+    for (int j = threadIdx.x; j < J; j += blockDim.x) {
+        const int item = b * J + j;
+        if (state[item].status != ST_NOROOT) {
+            sx += state[item].x / K;
+            ++nu;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sx += __shfl_down_sync(0xffffffffu, sx, off);
+        nu += __shfl_down_sync(0xffffffffu, nu, off);
+    }
+    if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = sx; red_n[threadIdx.x >> 5] = nu; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0; int n = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) { t += red[w]; n += red_n[w]; }
+        red[0] = t; red_n[0] = n;
+    }
+    __syncthreads();
+    const int n_used = red_n[0];
+    const double mean = n_used > 0 ? red[0] / n_used : 0.0;
+    bool use_mean = n_used < P;
+    if (!use_mean) {
+        const int npair = P * (P + 1) / 2;
+        for (int e = threadIdx.x; e < npair + P; e += blockDim.x) {
+            int r = 0, c = 0;
+            if (e < npair) {
+                int rem = e;
+                while (rem >= P - r) { rem -= P - r; ++r; }
+                c = r + rem;
+            } else {
+                r = e - npair;
+                c = -1;
+            }
+            double acc = 0.0;
+            for (int j = 0; j < J; ++j) {
+                const int item = b * J + j;
+                if (state[item].status == ST_NOROOT) continue;
+                const double* S = start + (size_t)item * d;
+                double y[MAXD];
+                int t = 0;
+                for (int q = 0; q < d; ++q)
+                    if (q != p) y[t++] = S[q] / K;
+                const double fr = basis_val(y, bi[r], bj[r]);
+                const double fc = c >= 0 ? basis_val(y, bi[c], bj[c]) : state[item].x / K;
+                acc += fr * fc;
+            }
+            if (c >= 0) { G[r * P + c] = acc; G[c * P + r] = acc; }
+            else rhs[r] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double dsc[MAXCOEF];
+            bool ok = true;
+            for (int i = 0; i < P; ++i) {
+                dsc[i] = G[i * P + i] > 0 ? 1.0 / sqrt(G[i * P + i]) : 0.0;
+                if (dsc[i] == 0.0) ok = false;
+            }
+            if (ok) {
+                for (int i = 0; i < P; ++i)
+                    for (int k = 0; k < P; ++k) G[i * P + k] *= dsc[i] * dsc[k];
+                // Cholesky G = R R^T (lower, in place)
+                for (int jj = 0; jj < P && ok; ++jj) {
+                    double v = G[jj * P + jj];
+                    for (int k = 0; k < jj; ++k) v -= G[jj * P + k] * G[jj * P + k];
+                    if (!(v > 1e-13)) { ok = false; break; }
+                    const double l = sqrt(v);
+                    G[jj * P + jj] = l;
+                    for (int i = jj + 1; i < P; ++i) {
+                        double w = G[i * P + jj];
+                        for (int k = 0; k < jj; ++k) w -= G[i * P + k] * G[jj * P + k];
+                        G[i * P + jj] = w / l;
+                    }
+                }
+            }
+            if (ok) {
+                double z[MAXCOEF];
+                for (int i = 0; i < P; ++i) {
+                    double v = rhs[i] * dsc[i];
+                    for (int k = 0; k < i; ++k) v -= G[i * P + k] * z[k];
+                    z[i] = v / G[i * P + i];
+                }
+                for (int i = P - 1; i >= 0; --i) {
+                    double v = z[i];
+                    for (int k = i + 1; k < P; ++k) v -= G[k * P + i] * coef[k];
+                    coef[i] = v / G[i * P + i];
+                }
+                for (int i = 0; i < P; ++i) coef[i] *= dsc[i];
+            } else {
+                for (int i = 0; i < P; ++i) coef[i] = 0.0;
+                coef[0] = mean;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (n_used == 0) {
+            for (int i = 0; i < P; ++i) coef[i] = 0.0;
+            coef[0] = M->payoff == BAP_BASKET_PUT ? -1.0 : 1e30;
+        } else if (use_mean) {
+            for (int i = 0; i < P; ++i) coef[i] = 0.0;
+            coef[0] = mean;
+        }
+        const size_t o = ((size_t)m * n_bnd + b) * P;
+        for (int i = 0; i < P; ++i) coef64[o + i] = coef[i];
+        stage_iz_one(coef64 + o, s, degree, K, coef_f + o, coef_d + o);
+        if (b == 0) fitted[m] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// CMC training points of date m: S = S_0 exp(mu t_m + sqrt(t_m) L z) with FP64 Box-Muller
+// normals of counter (j, 0, c, 0) under the TRAIN stream (reading of Section 3.3: independent
+// draws from the law of S_{t_m}).
+
+__global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int J, double* start,
+                                    int* ctr_item) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    const int d = M->d;
+    double z[MAXD + 3];
+    for (int c = 0; c < (d + 3) / 4; ++c) {
+        const uint4 x = philox((uint32_t)j, 0u, (uint32_t)c, 0u, rk);
+        double a0, a1;
+        PathMath<double>::box_muller(x.x, x.y, a0, a1);
+        z[4 * c] = a0;
+        z[4 * c + 1] = a1;
+        PathMath<double>::box_muller(x.z, x.w, a0, a1);
+        z[4 * c + 2] = a0;
+        z[4 * c + 3] = a1;
+    }
+    const double tm = M->t[m];
+    for (int q = 0; q < d; ++q) {
+        double wq = 0.0;
+        for (int i = 0; i <= q; ++i) wq += M->L[q * MAXD + i] * z[i];
+        const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+        start[(size_t)j * d + q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * wq);
+    }
+    ctr_item[j] = j;
+}
+
+// ---------------------------------------------------------------------------------------------
+// CMC rule staging for one date: constant stumps fold into F0; per feature the finite
+// thresholds sorted ascending and the step table T_f[c] = sum_{i<c} alpha_i pol_i -
+// sum_{i>=c} alpha_i pol_i, so F(S) = F0 + sum_f T_f[#{thresholds < x_f}].
+
+__device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr, const int* pol,
+                              const double* alpha, int rec_len, float* rf, double* rd) {
+    for (int i = 0; i < rec_len; ++i) { rf[i] = 0.f; rd[i] = 0.0; }
+    double F0 = 0.0;
+    for (int i = 0; i < ns; ++i)
+        if (isinf(thr[i]) && thr[i] < 0) F0 += alpha[i] * pol[i];
+    rf[0] = (float)F0;
+    rd[0] = F0;
+    int off = 2 + 2 * nF;
+    for (int f = 0; f < nF; ++f) {
+        int idx[BAP_MAX_STUMPS];
+        int n = 0;
+        for (int i = 0; i < ns; ++i)
+            if (feat[i] == f && !(isinf(thr[i]) && thr[i] < 0)) {
+                int k = n++;
+                while (k > 0 && thr[idx[k - 1]] > thr[i]) { idx[k] = idx[k - 1]; --k; }
+                idx[k] = i;
+            }
+        rf[2 + f] = __int_as_float(n);
+        rd[2 + f] = __longlong_as_double((long long)n);
+        rf[2 + nF + f] = __int_as_float(off);
+        rd[2 + nF + f] = __longlong_as_double((long long)off);
+        if (n == 0) continue;
+        double tot = 0.0;
+        for (int i = 0; i < n; ++i) tot += alpha[idx[i]] * pol[idx[i]];
+        double pre = 0.0;
+        for (int c = 0; c <= n; ++c) {
+            if (c < n) {
+                rf[off + c] = (float)thr[idx[c]];
+                rd[off + c] = thr[idx[c]];
+            }
+            const double T = 2.0 * pre - tot;
+            rf[off + n + c] = (float)T;
+            rd[off + n + c] = T;
+            if (c < n) pre += alpha[idx[c]] * pol[idx[c]];
+        }
+        off += 2 * n + 1;
+    }
+}
+
+__global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int* n_stumps,
+                                 const int* feat, const double* thr, const int* pol,
+                                 const double* alpha, int rec_len, float* rec_f, double* rec_d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_dates) return;
+    const size_t o = (size_t)k * max_stumps;
+    stage_cmc_one(nF, n_stumps[k], feat + o, thr + o, pol + o, alpha + o, rec_len,
+                  rec_f + (size_t)k * rec_len, rec_d + (size_t)k * rec_len);
+}
+
+// ---------------------------------------------------------------------------------------------
+// [class] Discrete AdaBoost on stumps for date m, one block (Section 3.2 names AdaBoost).
+// Features: the d prices and Phi.  Candidates per feature, in order: the constant stump
+// (threshold below every value; polarity +1 then -1), then the midpoints between consecutive
+// distinct sorted values (polarity +1 then -1); with e_min the least weighted error the first
+// candidate with error <= e_min + 1e-12 wins.  alpha = 1/2 ln((1-eps)/eps) with eps clamped to
+// [1e-10, 1-1e-10]; stop before a stump with eps >= 1/2 and after a perfect one.
+
+__device__ inline bool key_less(double a, int ia, double b, int ib) {
+    return a < b || (a == b && ia < ib);
+}
+
+__global__ void __launch_bounds__(1024) adaboost_kernel(
+    const DevModel* M, int m, int J, const double* X, const double* label_y, const int* label,
+    int n_rounds, double* sorted_v, int* sorted_i, double* err, int max_stumps, int* n_stumps,
+    int* feat, double* thr, int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d,
+    int* fitted) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int d = M->d;
+    const int nF = d + 1;
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    double* w = reinterpret_cast<double*>(smem);          // J
+    double* key = w + J;                                  // P2
+    int* idx = reinterpret_cast<int*>(key + P2);          // P2
+    __shared__ double wred[32];
+    __shared__ double fmin_e[MAXF];
+    __shared__ long long fcand[MAXF];
+    __shared__ double s_W, s_neg[MAXF], s_alpha, s_thr, s_e;
+    __shared__ int s_f, s_pol, s_stop, s_count;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const unsigned FULL = 0xffffffffu;
+
+    // The payoff feature Phi(x_i) is recomputed in FP64 from the point (the same definition as
+    // the label epilogue of the path kernel).
+    // sort each feature (bitonic on (value, index))
+    for (int f = 0; f < nF; ++f) {
+        for (int i = tid; i < P2; i += blockDim.x) {
+            if (i < J) {
+                double v;
+                if (f < d) {
+                    v = X[(size_t)i * d + f];
+                } else {
+                    const double* S = X + (size_t)i * d;
+                    if (M->payoff == BAP_MAX_CALL) {
+                        double mx = S[0];
+                        for (int q = 1; q < d; ++q) mx = S[q] > mx ? S[q] : mx;
+                        v = mx - M->K;
+                    } else if (M->payoff == BAP_BASKET_PUT) {
+                        double b = 0;
+                        for (int q = 0; q < d; ++q) b += M->w[q] * S[q];
+                        v = M->K - b;
+                    } else {
+                        double lg = 0;
+                        for (int q = 0; q < d; ++q) lg += M->w[q] * log(S[q]);
+                        v = exp(lg) - M->K;
+                    }
+                    v = v > 0 ? v : 0;
+                }
+                key[i] = v;
+                idx[i] = i;
+            } else {
+                key[i] = INFINITY;
+                idx[i] = 0x7fffffff;
+            }
+        }
+        __syncthreads();
+        for (int size = 2; size <= P2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = tid; i < P2; i += blockDim.x) {
+                    const int jx = i ^ stride;
+                    if (jx > i) {
+                        const bool up = (i & size) == 0;
+                        const bool lt = key_less(key[jx], idx[jx], key[i], idx[i]);
+                        if (lt == up) {
+                            const double tk = key[i]; key[i] = key[jx]; key[jx] = tk;
+                            const int ti = idx[i]; idx[i] = idx[jx]; idx[jx] = ti;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < J; i += blockDim.x) {
+            sorted_v[(size_t)f * J + i] = key[i];
+            sorted_i[(size_t)f * J + i] = idx[i];
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < J; i += blockDim.x) w[i] = 1.0 / (double)J;
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+
+    const size_t o_st = (size_t)m * max_stumps;
+    for (int round = 0; round < n_rounds; ++round) {
+        // W = sum of weights
+        double part = 0.0;
+        for (int i = tid; i < J; i += blockDim.x) part += w[i];
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(FULL, part, off);
+        if (lane == 0) wred[wid] = part;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k) t += wred[k];
+            s_W = t;
+        }
+        __syncthreads();
+        const double W = s_W;
+        // pass 1: one warp per feature scans its sorted order
+        for (int f = wid; f < nF; f += nw) {
+            const double* v = sorted_v + (size_t)f * J;
+            const int* ix = sorted_i + (size_t)f * J;
+            double neg = 0.0;
+            for (int i = lane; i < J; i += 32) neg += label[ix[i]] < 0 ? w[ix[i]] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) neg += __shfl_down_sync(FULL, neg, off);
+            neg = __shfl_sync(FULL, neg, 0);
+            double cpos = 0.0, cneg = 0.0;      // running prefix carried across chunks
+            double emin = fmin(neg, W - neg);
+            for (int base = 0; base < J; base += 32) {
+                const int i = base + lane;
+                double ap = 0.0, an = 0.0;
+                if (i < J) {
+                    const double wi = w[ix[i]];
+                    if (label[ix[i]] > 0) ap = wi; else an = wi;
+                }
+                for (int off = 1; off < 32; off <<= 1) {
+                    const double tp = __shfl_up_sync(FULL, ap, off);
+                    const double tn = __shfl_up_sync(FULL, an, off);
+                    if (lane >= off) { ap += tp; an += tn; }
+                }
+                ap += cpos;
+                an += cneg;
+                double e = NAN;
+                if (i < J - 1 && v[i + 1] > v[i]) {
+                    e = ap + (neg - an);
+                    emin = fmin(emin, fmin(e, W - e));
+                }
+                if (i < J - 1) err[(size_t)f * J + i] = e;
+                cpos = __shfl_sync(FULL, ap, 31);
+                cneg = __shfl_sync(FULL, an, 31);
+            }
+            for (int off = 16; off > 0; off >>= 1) emin = fmin(emin, __shfl_down_sync(FULL, emin, off));
+            if (lane == 0) { fmin_e[f] = emin; s_neg[f] = neg; }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double e = INFINITY;
+            for (int f = 0; f < nF; ++f) e = fmin(e, fmin_e[f]);
+            s_e = e;
+        }
+        __syncthreads();
+        const double lim = s_e + 1e-12;
+        // pass 2: first candidate within the tie tolerance, per feature
+        for (int f = wid; f < nF; f += nw) {
+            const double neg = s_neg[f];
+            long long cand = LLONG_MAX;
+            if (neg <= lim) cand = 0;
+            else if (W - neg <= lim) cand = 1;
+            else {
+                for (int base = 0; base < J - 1 && cand == LLONG_MAX; base += 32) {
+                    const int i = base + lane;
+                    long long c = LLONG_MAX;
+                    if (i < J - 1) {
+                        const double e = err[(size_t)f * J + i];
+                        if (!isnan(e)) {
+                            if (e <= lim) c = 2 + 2LL * i;
+                            else if (W - e <= lim) c = 3 + 2LL * i;
+                        }
+                    }
+                    for (int off = 16; off > 0; off >>= 1) c = min(c, __shfl_down_sync(FULL, c, off));
+                    cand = __shfl_sync(FULL, c, 0);
+                }
+            }
+            if (lane == 0) fcand[f] = cand;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int f = 0;
+            while (f < nF && fcand[f] == LLONG_MAX) ++f;
+            if (f == nF) f = 0;   // cannot happen: the minimum is always a candidate
+            const long long c = fcand[f];
+            double e, th;
+            int pl;
+            if (c < 2) {
+                th = -INFINITY;
+                pl = c == 0 ? 1 : -1;
+                e = c == 0 ? s_neg[f] : W - s_neg[f];
+            } else {
+                const int i = (int)((c - 2) / 2);
+                pl = ((c - 2) % 2 == 0) ? 1 : -1;
+                const double ep = err[(size_t)f * J + i];
+                e = pl > 0 ? ep : W - ep;
+                th = 0.5 * (sorted_v[(size_t)f * J + i] + sorted_v[(size_t)f * J + i + 1]);
+            }
+            const double eps = e / W;
+            s_stop = 0;
+            if (eps >= 0.5 - 1e-12) {
+                s_stop = 1;
+            } else {
+                const double ec = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);
+                const double al = 0.5 * log((1.0 - ec) / ec);
+                const int k = s_count++;
+                feat[o_st + k] = f;
+                thr[o_st + k] = th;
+                pol[o_st + k] = pl;
+                alpha[o_st + k] = al;
+                s_f = f; s_thr = th; s_pol = pl; s_alpha = al;
+                if (eps <= 1e-10) s_stop = 2;
+            }
+        }
+        __syncthreads();
+        if (s_stop == 1) break;
+        // weight update w_i <- w_i exp(-alpha y_i h(x_i)), then normalise
+        {
+            const int f = s_f;
+            const double th = s_thr, al = s_alpha;
+            const int pl = s_pol;
+            double part2 = 0.0;
+            // h(x_i) through the sorted order of feature f, which holds the feature values
+            const double* sv = sorted_v + (size_t)f * J;
+            const int* si = sorted_i + (size_t)f * J;
+            for (int r = tid; r < J; r += blockDim.x) {
+                const int i = si[r];
+                const double h = sv[r] > th ? (double)pl : (double)-pl;
+                w[i] = w[i] * exp(-al * (double)label[i] * h);
+            }
+            __syncthreads();
+            for (int i = tid; i < J; i += blockDim.x) part2 += w[i];
+            for (int off = 16; off > 0; off >>= 1) part2 += __shfl_down_sync(FULL, part2, off);
+            if (lane == 0) wred[wid] = part2;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int k = 0; k < nw; ++k) t += wred[k];
+                s_W = t;
+            }
+            __syncthreads();
+            const double Wn = s_W;
+            for (int i = tid; i < J; i += blockDim.x) w[i] = w[i] / Wn;
+            __syncthreads();
+        }
+        if (s_stop == 2) break;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        n_stumps[m] = s_count;
+        stage_cmc_one(nF, s_count, feat + o_st, thr + o_st, pol + o_st, alpha + o_st, rec_len,
+                      rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
+        fitted[m] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Small helpers.
+
+__global__ void set_int_kernel(int* p, int v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+__global__ void copy_s0_kernel(const DevModel* M, double* start) {
+    const int q = threadIdx.x;
+    if (q < M->d) start[q] = M->S0[q];
+}
+
+__global__ void rng_debug_kernel(RoundKeys rk, uint32_t w1, uint32_t step, int d, long long count,
+                                 uint32_t* words, double* z) {
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= count) return;
+    const int nc = (d + 3) / 4;
+    for (int c = 0; c < nc; ++c) {
+        const uint4 x = philox((uint32_t)n, w1, 4u * step + (uint32_t)c, 0u, rk);
+        if (words) {
+            uint32_t* wo = words + ((size_t)n * nc + c) * 4;
+            wo[0] = x.x; wo[1] = x.y; wo[2] = x.z; wo[3] = x.w;
+        }
+        if (z) {
+            float a0, a1;
+            PathMath<float>::box_muller(x.x, x.y, a0, a1);
+            if (4 * c < d) z[(size_t)n * d + 4 * c] = a0;
+            if (4 * c + 1 < d) z[(size_t)n * d + 4 * c + 1] = a1;
+            PathMath<float>::box_muller(x.z, x.w, a0, a1);
+            if (4 * c + 2 < d) z[(size_t)n * d + 4 * c + 2] = a0;
+            if (4 * c + 3 < d) z[(size_t)n * d + 4 * c + 3] = a1;
+        }
+    }
+}
+
+// Counts of items by status (for n_noconv / n_noroot) and the per-date diagnostics copy.
+__global__ void collect_points_kernel(const ItemState* state, int n, double* x_out, int* it_out,
+                                      int* st_out, int* counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const ItemState s = state[i];
+    x_out[i] = s.x;
+    it_out[i] = s.iters;
+    st_out[i] = s.status;
+    if (s.status == ST_NOCONV) atomicAdd(&counts[0], 1);
+    if (s.status == ST_NOROOT) atomicAdd(&counts[1], 1);
+}
+
+__global__ void collect_labels_kernel(const double* label_y, int n, double* x_out, int* it_out,
+                                      int* st_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x_out[i] = label_y[i];
+    it_out[i] = 1;
+    st_out[i] = 0;
+}
+
+}  // namespace bap

@@ -1,0 +1,40 @@
+// bap_fit.cuh -- declarations of the device kernels around the path kernel (bap_fit.cu).
+#pragma once
+
+#include "bap_internal.cuh"
+
+namespace bap {
+
+__global__ void model_setup_kernel(DevModel* M, const double* rho, int* status);
+__global__ void korobov_merit_kernel(int J, int s, double* merit);
+__global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_a);
+__global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
+                                double* start, ItemState* state, int* pivot, int* active,
+                                int* count);
+__global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
+                                int degree, double K, float* coef_f, double* coef_d);
+__global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
+                              const double* start, const ItemState* state, double* coef64,
+                              float* coef_f, double* coef_d, int* fitted);
+__global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int J, double* start,
+                                    int* ctr_item);
+__global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int* n_stumps,
+                                 const int* feat, const double* thr, const int* pol,
+                                 const double* alpha, int rec_len, float* rec_f, double* rec_d);
+__global__ void adaboost_kernel(const DevModel* M, int m, int J, const double* X,
+                                const double* label_y, const int* label, int n_rounds,
+                                double* sorted_v, int* sorted_i, double* err, int max_stumps,
+                                int* n_stumps, int* feat, double* thr, int* pol, double* alpha,
+                                int rec_len, float* rec_f, double* rec_d, int* fitted);
+__global__ void set_int_kernel(int* p, int v);
+__global__ void copy_s0_kernel(const DevModel* M, double* start);
+__global__ void rng_debug_kernel(RoundKeys rk, uint32_t w1, uint32_t step, int d, long long count,
+                                 uint32_t* words, double* z);
+__global__ void collect_points_kernel(const ItemState* state, int n, double* x_out, int* it_out,
+                                      int* st_out, int* counts);
+__global__ void collect_labels_kernel(const double* label_y, int n, double* x_out, int* it_out,
+                                      int* st_out);
+
+template <int D> const void* path_kernel_fn(int rule, bool fp64);
+
+}  // namespace bap

@@ -1,0 +1,168 @@
+// bap_internal.cuh -- device-side structures and building blocks of the nested Monte Carlo
+// library (Doan et al., INRIA RR-6530, 2008).  Private to the library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bap.h"
+
+namespace bap {
+
+constexpr int MAXD = BAP_MAX_D;
+constexpr int MAXF = MAXD + 1;            // CMC features: d prices + the payoff
+constexpr int MAXDATES = BAP_MAX_DATES;
+constexpr int MAXCOEF = 1 + (MAXD - 1) + (MAXD - 1) * MAXD / 2;   // quadratic in d-1 variables
+constexpr int WARP = 32;
+
+enum Purpose : uint32_t { P_IZ = 1, P_CMC = 2, P_TRAIN = 3, P_PRICE = 4 };
+enum RuleKind : int { R_NONE = 0, R_IZ = 1, R_CMC = 2 };
+enum Mode : int { MODE_SUMS = 0, MODE_NEWTON = 1, MODE_LABEL = 2, MODE_TRACE = 3 };
+enum ItemStatus : int { ST_OK = 0, ST_NOCONV = 1, ST_NOROOT = 2 };
+
+// Market model in device memory: FP64 master values and the per-date stepping constants in
+// log2 units, in FP32 and FP64 (Section 2.2: correlated GBM, rate r, yields delta_i).
+struct DevModel {
+    int d, n_dates, payoff, uniform_dates;
+    double r, K;
+    double S0[MAXD], sigma[MAXD], delta[MAXD], w[MAXD];
+    double t[MAXDATES + 1];
+    double L[MAXD * MAXD];                 // lower Cholesky factor of rho, FP64
+    double drift2[MAXDATES + 1][MAXD];     // (r - delta_q - sigma_q^2/2) (t_k - t_{k-1}) / ln 2
+    double vol2[MAXDATES + 1][MAXD];       // sigma_q sqrt(t_k - t_{k-1}) / ln 2
+};
+
+// Newton state of one I&Z boundary point (FP64, Section 2.3 "Newton's iterations").
+struct ItemState {
+    double x, lo, hi, dx_old, dx;
+    int iters, status, done, pivot;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds; multipliers 0xD2511F53 and
+// 0xCD9E8D57; Weyl key increments 0x9E3779B9 and 0xBB67AE85.  Round keys are precomputed once
+// per launch (key = (lo32(seed), hi32(seed) ^ purpose << 24 ^ m)).
+
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint64_t seed, uint32_t purpose, uint32_t m) {
+    RoundKeys rk;
+    uint32_t a = (uint32_t)(seed & 0xffffffffu);
+    uint32_t b = (uint32_t)(seed >> 32) ^ (purpose << 24) ^ m;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = a;
+        rk.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        const RoundKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t n0 = hi1 ^ c1 ^ rk.k0[r];
+        uint32_t n2 = hi0 ^ c3 ^ rk.k1[r];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Single-precision hardware approximations (PTX .approx instructions) and their FP64
+// counterparts, selected by the path arithmetic type.
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <typename Real> struct PathMath;
+
+template <> struct PathMath<float> {
+    __device__ __forceinline__ static float exp2r(float x) { return ex2_approx(x); }
+    // Box-Muller pair from two Philox words: u1 = (v0 + 1) 2^-23, u2 = v1 2^-23.  The angle is
+    // taken as 2 pi (u2 - 1/2) in [-pi, pi) (the hardware sine's accurate range) and the sign
+    // folded into the radius: cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), same for sin.
+    __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
+                                                      float& z1) {
+        float u1 = __uint_as_float(0x3f800000u | (w0 >> 9)) - 0.99999988079071044921875f;
+        float u2c = __uint_as_float(0x3f800000u | (w1 >> 9)) - 1.5f;
+        float r = -sqrt_approx(-1.3862943611198906f * lg2_approx(u1));   // -sqrt(-2 ln u1)
+        float a = 6.283185307179586f * u2c;
+        z0 = r * __cosf(a);
+        z1 = r * __sinf(a);
+    }
+};
+
+template <> struct PathMath<double> {
+    __device__ __forceinline__ static double exp2r(double x) { return exp2(x); }
+    __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, double& z0,
+                                                      double& z1) {
+        double u1 = (double)((w0 >> 9) + 1u) * (1.0 / 8388608.0);
+        double u2 = (double)(w1 >> 9) * (1.0 / 8388608.0);
+        double r = sqrt(-2.0 * log(u1));
+        double s, c;
+        sincospi(2.0 * u2, &s, &c);
+        z0 = r * c;
+        z1 = r * s;
+    }
+};
+
+// The D normals of counter prefix (w0, w1, 4*step): Philox call c gives normals 4c..4c+3,
+// words (0,1) -> (cos, sin) pair 0 and words (2,3) -> pair 1.
+template <int D, typename Real>
+__device__ __forceinline__ void normals(uint32_t w0, uint32_t w1, uint32_t step,
+                                        const RoundKeys& rk, Real (&z)[D]) {
+#pragma unroll
+    for (int c = 0; c < (D + 3) / 4; ++c) {
+        uint4 x = philox(w0, w1, 4u * step + (uint32_t)c, 0u, rk);
+        Real a, b;
+        if (4 * c < D) {
+            PathMath<Real>::box_muller(x.x, x.y, a, b);
+            z[4 * c] = a;
+            if (4 * c + 1 < D) z[4 * c + 1] = b;
+        }
+        if (4 * c + 2 < D) {
+            PathMath<Real>::box_muller(x.z, x.w, a, b);
+            z[4 * c + 2] = a;
+            if (4 * c + 3 < D) z[4 * c + 3] = b;
+        }
+    }
+}
+
+__host__ __device__ inline int n_basis(int s, int degree) {
+    int n = 1;
+    if (degree >= 1) n += s;
+    if (degree >= 2) n += s * (s + 1) / 2;
+    return n;
+}
+
+// CMC staged rule record per date (floats or doubles; counts and offsets stored as values):
+// [0] F0 = sum of the constant stumps' votes, [1] spare, [2..2+nF) stump count per feature,
+// [2+nF..2+2nF) offset of the feature's sorted thresholds within the record; the step table
+// T_f[0..n_f] follows the thresholds.  F(S) = F0 + sum_f T_f[#{thresholds < x_f}].
+__host__ __device__ inline int cmc_record_len(int nF, int max_stumps) {
+    return 2 + 3 * nF + 2 * max_stumps;
+}
+
+}  // namespace bap

@@ -1,0 +1,491 @@
+// bap_path.cuh -- the nested Monte Carlo path kernel (the hot path).
+//
+// One launch evaluates continuation sums for a list of items (I&Z boundary points or their
+// Newton iterates, CMC training points, or the single pricing start point).  Section 2.2:
+// "these optimal boundary points are computed using N_1 MC simulations"; Section 3.2: "From
+// each price point, another N_2 paths are simulated ... to compute the small BA option price".
+//
+// Work decomposition: an item's N paths are cut into chunks of `chunk` paths; a (item, chunk)
+// unit belongs to one warp, taken from a device counter (persistent grid).  Inside a warp every
+// lane runs one path at a time and takes the next path index of the chunk as soon as its path
+// stops (warp ballot), so early-stopped paths leave no idle lanes.  Results per unit are summed
+// per lane (FP32, flushed to FP64 every 16 paths), reduced across the warp in a fixed shuffle
+// tree and written to a fixed slot; the warp that completes an item's last unit sums the slots
+// in fixed order, so results are bitwise reproducible whatever the scheduling.  That warp then
+// runs the item's epilogue on the device: the Newton update of an I&Z boundary point (and its
+// re-queueing), the CMC label, or the plain sums.
+#pragma once
+
+#include "bap_internal.cuh"
+
+namespace bap {
+
+struct PathArgs {
+    const DevModel* model;
+    int m;                       // paths start at t_m and run over t_{m+1}..t_NT
+    int mode;                    // Mode
+    int n_dates, payoff, uniform;
+    double r, K;
+    float Lf[MAXD * MAXD];       // vol-scaled Cholesky factor (uniform dates) or plain L
+    double Ld[MAXD * MAXD];
+    float driftf[MAXD];          // uniform dates: per-step log2 drift
+    double driftd[MAXD];
+    float wf[MAXD];              // basket / geometric weights
+    RoundKeys rk;
+    int64_t N;                   // paths per item
+    int chunk;                   // paths per unit (multiple of 32)
+    int C;                       // units per item
+    const int* active;           // item list (nullptr: item = slot)
+    const int* n_active;         // device count of the list
+    unsigned long long* work;    // unit counter (zeroed before the launch)
+    double* start;               // items x d start points (FP64); Newton writes the pivot value
+    const int* ctr_item;         // Philox counter word 1 per item (nullptr: 0)
+    const int* pivot;            // pivot asset per item for the pathwise derivative (or nullptr)
+    double* partial;             // items x C x 3
+    long long* partial_steps;    // items x C
+    int* done;                   // per item: units finished in the current pass
+    unsigned long long* total_steps;
+    // rule
+    int rule_kind;
+    const void* rule_src;        // staged rule table (Real), dates 0..n_dates
+    int rule_stride;             // Reals per date
+    int n_bnd, n_coef, degree;
+    const int* fitted;           // n_dates + 1
+    // epilogues
+    double* out_sums;            // MODE_SUMS / MODE_TRACE: items x 3
+    long long* out_steps;
+    int* trace_tau;              // MODE_TRACE: per path
+    double* trace_phi;
+    ItemState* state;            // MODE_NEWTON
+    int* next_active;
+    int* next_count;
+    double f_tol, x_tol, fp_eps;
+    int max_iter, fixed_point;
+    double* label_y;             // MODE_LABEL: Phi - C
+    int* label;                  // +1 exercise / -1 continue
+};
+
+// ---------------------------------------------------------------------------------------------
+// FP64 payoff at a start point (the item's own point; used by the Newton and label epilogues).
+
+__device__ inline double payoff64(const PathArgs& a, const double* S, int d) {
+    if (a.payoff == BAP_MAX_CALL) {
+        double mx = S[0];
+        for (int q = 1; q < d; ++q) mx = S[q] > mx ? S[q] : mx;
+        double v = mx - a.K;
+        return v > 0 ? v : 0;
+    } else if (a.payoff == BAP_BASKET_PUT) {
+        double b = 0;
+        for (int q = 0; q < d; ++q) b += a.model->w[q] * S[q];
+        double v = a.K - b;
+        return v > 0 ? v : 0;
+    }
+    double lg = 0;
+    for (int q = 0; q < d; ++q) lg += a.model->w[q] * log(S[q]);
+    double v = exp(lg) - a.K;
+    return v > 0 ? v : 0;
+}
+
+// dPhi/dS_p * S_p at S (zero out of the money).
+__device__ inline double payoff_dlog64(const PathArgs& a, const double* S, int d, int p) {
+    double phi = payoff64(a, S, d);
+    if (phi <= 0) return 0;
+    if (a.payoff == BAP_MAX_CALL) {
+        int best = 0;
+        for (int q = 1; q < d; ++q)
+            if (S[q] > S[best]) best = q;
+        return best == p ? S[p] : 0.0;
+    }
+    if (a.payoff == BAP_BASKET_PUT) return -a.model->w[p] * S[p];
+    return a.model->w[p] * (phi + a.K);
+}
+
+// Newton update of one boundary point after an evaluation of C(x) and C'(x) (FP64; the same
+// safeguarded iteration as the reference description: bracket from the signs seen, Newton step
+// unless it leaves the bracket or fails to halve the step before last, else bisection, or
+// doubling while no upper end is known).  Returns true if the item needs another evaluation.
+__device__ inline bool newton_update(const PathArgs& a, int item, double C, double dC) {
+    const int d = a.model->d;
+    ItemState& s = a.state[item];
+    double* S = a.start + (size_t)item * d;
+    const int p = s.pivot;
+    const double K = a.K;
+    double x = s.x;
+    s.iters += 1;
+    const double phi = payoff64(a, S, d);
+    const double f = phi - C;
+    const bool put_like = a.payoff == BAP_BASKET_PUT;
+    bool done = false;
+    double xn = x;
+    if (a.fixed_point) {
+        if (a.payoff == BAP_MAX_CALL) {
+            xn = K + C;
+        } else if (a.payoff == BAP_GEO_CALL) {
+            double lg = log(K + C);
+            for (int q = 0; q < d; ++q)
+                if (q != p) lg -= a.model->w[q] * log(S[q]);
+            xn = exp(lg / a.model->w[p]);
+        } else {
+            double v = K - C;
+            for (int q = 0; q < d; ++q)
+                if (q != p) v -= a.model->w[q] * S[q];
+            xn = v / a.model->w[p];
+            if (xn < 0) xn = 0;
+        }
+        if (fabs(xn - x) < a.fp_eps) done = true;
+        x = xn;
+    } else if (fabs(f) < a.f_tol) {
+        done = true;
+    } else {
+        const double dphi = payoff_dlog64(a, S, d, p) / x;
+        const double fp = dphi - dC;
+        const double sg = put_like ? -1.0 : 1.0;
+        const double g = sg * f, gp = sg * fp;
+        if (g < 0) s.lo = x; else s.hi = x;
+        const double tol = a.x_tol * (fabs(x) > 1.0 ? fabs(x) : 1.0);
+        if (s.hi - s.lo <= tol) {
+            done = true;
+        } else {
+            xn = x - g / gp;
+            const bool ok = gp > 0 && xn > s.lo && xn < s.hi && fabs(2.0 * g) <= fabs(s.dx_old * gp);
+            if (!ok) xn = isinf(s.hi) ? 2.0 * x : 0.5 * (s.lo + s.hi);
+            s.dx_old = s.dx;
+            s.dx = xn - x;
+            if (xn > 1e3 * K) {
+                x = 1e3 * K;
+                s.status = ST_NOROOT;
+                done = true;
+            } else if (xn < 1e-6 * K) {
+                x = 0.0;
+                s.status = ST_NOROOT;
+                done = true;
+            } else if (fabs(s.dx) <= tol) {
+                x = xn;
+                done = true;
+            } else {
+                x = xn;
+            }
+        }
+    }
+    if (!done && s.iters >= a.max_iter) {
+        s.status = ST_NOCONV;
+        done = true;
+    }
+    s.x = x;
+    S[p] = x;
+    s.done = done ? 1 : 0;
+    return !done;
+}
+
+// ---------------------------------------------------------------------------------------------
+
+template <int D, int RULE, typename Real>
+__global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NF = D + 1;
+    const int nk = a.n_dates - a.m;                  // dates m+1..NT
+    Real* sh_disc = reinterpret_cast<Real*>(smem_raw);
+    Real* sh_drift = sh_disc + nk;                   // non-uniform dates: [nk][D]
+    Real* sh_vol = sh_drift + (a.uniform ? 0 : nk * D);
+    Real* sh_rule = sh_vol + (a.uniform ? 0 : nk * D);
+    const int n_rule_dates = nk - 1;                 // fitted dates m+1..NT-1
+    const int rule_len = (RULE == R_NONE) ? 0 : n_rule_dates * a.rule_stride;
+    int* sh_fit = reinterpret_cast<int*>(sh_rule + rule_len);
+
+    const DevModel* M = a.model;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+        const int k = a.m + 1 + i;
+        sh_disc[i] = (Real)exp(-a.r * (M->t[k] - M->t[a.m]));
+        sh_fit[i] = (a.fitted != nullptr && k < a.n_dates) ? a.fitted[k] : 0;
+    }
+    if (!a.uniform) {
+        for (int i = threadIdx.x; i < nk * D; i += blockDim.x) {
+            const int k = a.m + 1 + i / D, q = i % D;
+            sh_drift[i] = (Real)M->drift2[k][q];
+            sh_vol[i] = (Real)M->vol2[k][q];
+        }
+    }
+    if (RULE != R_NONE) {
+        const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
+        for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
+    }
+    __syncthreads();
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const long long total_units = (long long)(*a.n_active) * a.C;
+    const Real K = (Real)a.K;
+    const bool is_put = a.payoff == BAP_BASKET_PUT;
+    const bool is_max = a.payoff == BAP_MAX_CALL;
+    const bool is_geo = a.payoff == BAP_GEO_CALL;
+
+    Real Lr[D * (D + 1) / 2];
+    Real drift_u[D];
+#pragma unroll
+    for (int q = 0, o = 0; q < D; ++q)
+#pragma unroll
+        for (int j = 0; j <= q; ++j, ++o) Lr[o] = sizeof(Real) == 4 ? (Real)a.Lf[q * MAXD + j] : (Real)a.Ld[q * MAXD + j];
+#pragma unroll
+    for (int q = 0; q < D; ++q) drift_u[q] = sizeof(Real) == 4 ? (Real)a.driftf[q] : (Real)a.driftd[q];
+
+    while (true) {
+        unsigned long long unit_u = 0;
+        if (lane == 0) unit_u = atomicAdd(a.work, 1ULL);
+        const long long unit = (long long)__shfl_sync(FULL, unit_u, 0);
+        if (unit >= total_units) break;
+        const int slot = (int)(unit / a.C);
+        const int chunk = (int)(unit - (long long)slot * a.C);
+        const int item = a.active ? a.active[slot] : slot;
+
+        const double* st = a.start + (size_t)item * D;
+        Real l0[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) l0[q] = (Real)log2(st[q]);
+        const uint32_t item_word = a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u;
+        const int pivot = a.pivot ? a.pivot[item] : -1;
+        const long long n_begin = (long long)chunk * a.chunk;
+        const long long n_end = min((long long)a.N, n_begin + a.chunk);
+
+        long long n = n_begin + lane;
+        bool has = n < n_end;
+        long long next = n_begin + 32;
+        Real l[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) l[q] = l0[q];
+        int k = a.m;
+        Real acc0 = 0, acc1 = 0, acc2 = 0;
+        double s0 = 0, s1 = 0, s2 = 0;
+        int since_flush = 0;
+        long long steps = 0;
+
+        while (__any_sync(FULL, has)) {
+            bool finished = false;
+            if (has) {
+                k += 1;
+                ++steps;
+                Real z[D];
+                normals<D, Real>((uint32_t)n, item_word + (uint32_t)(n >> 32), (uint32_t)k, a.rk, z);
+                if (a.uniform) {
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        const int o = q * (q + 1) / 2;
+                        Real wq = 0;
+#pragma unroll
+                        for (int j = 0; j <= q; ++j) wq = fma(Lr[o + j], z[j], wq);
+                        l[q] = l[q] + drift_u[q] + wq;
+                    }
+                } else {
+                    const int kk = (k - a.m - 1) * D;
+#pragma unroll
+                    for (int q = 0; q < D; ++q) {
+                        const int o = q * (q + 1) / 2;
+                        Real wq = 0;
+#pragma unroll
+                        for (int j = 0; j <= q; ++j) wq = fma(Lr[o + j], z[j], wq);
+                        l[q] = fma(sh_vol[kk + q], wq, l[q] + sh_drift[kk + q]);
+                    }
+                }
+                // prices and payoff
+                Real S[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) S[q] = PathMath<Real>::exp2r(l[q]);
+                int imax = 0;
+                Real lmax = l[0];
+#pragma unroll
+                for (int q = 1; q < D; ++q)
+                    if (l[q] > lmax) { lmax = l[q]; imax = q; }
+                Real phi;
+                Real gval = 0;
+                if (is_max) {
+                    Real smax = S[0];
+#pragma unroll
+                    for (int q = 1; q < D; ++q) smax = (q == imax) ? S[q] : smax;
+                    phi = smax - K;
+                } else if (is_put) {
+                    Real b = 0;
+#pragma unroll
+                    for (int q = 0; q < D; ++q) b = fma((Real)a.wf[q], S[q], b);
+                    phi = K - b;
+                } else {
+                    Real lg = 0;
+#pragma unroll
+                    for (int q = 0; q < D; ++q) lg = fma((Real)a.wf[q], l[q], lg);
+                    gval = PathMath<Real>::exp2r(lg);
+                    phi = gval - K;
+                }
+                bool ex = phi > 0;
+                if (ex && k < a.n_dates) {
+                    const int kr = k - a.m - 1;
+                    if (RULE == R_NONE || !sh_fit[kr]) {
+                        ex = false;
+                    } else if (RULE == R_IZ) {
+                        const int p = is_max ? imax : 0;
+                        Real sp = S[0];
+#pragma unroll
+                        for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
+                        const Real* c = sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * a.n_coef;
+                        Real B = c[0];
+                        if (D > 1) {
+                            Real y[D > 1 ? D - 1 : 1];
+#pragma unroll
+                            for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
+                            if (a.degree == 2) {
+                                int idx = 1;
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) {
+                                    Real acc = c[idx++];
+#pragma unroll
+                                    for (int u = t; u < D - 1; ++u) acc = fma(c[idx++], y[u], acc);
+                                    B = fma(acc, y[t], B);
+                                }
+                            } else if (a.degree == 1) {
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) B = fma(c[1 + t], y[t], B);
+                            }
+                        }
+                        ex = is_put ? (sp <= B) : (sp >= B);
+                    } else {  // R_CMC
+                        const Real* rec = sh_rule + kr * a.rule_stride;
+                        Real F = rec[0];
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            int nf, off;
+                            if (sizeof(Real) == 4) {
+                                nf = __float_as_int((float)rec[2 + f]);
+                                off = __float_as_int((float)rec[2 + NF + f]);
+                            } else {
+                                nf = (int)__double_as_longlong((double)rec[2 + f]);
+                                off = (int)__double_as_longlong((double)rec[2 + NF + f]);
+                            }
+                            if (nf > 0) {
+                                Real xv = phi;
+#pragma unroll
+                                for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
+                                int lo = 0, hi = nf;
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (rec[off + mid] < xv) lo = mid + 1; else hi = mid;
+                                }
+                                F += rec[off + nf + lo];
+                            }
+                        }
+                        ex = F > 0;
+                    }
+                }
+                if (ex || k == a.n_dates) {
+                    finished = true;
+                    Real v = 0, dv = 0;
+                    if (ex) {
+                        const Real disc = sh_disc[k - a.m - 1];
+                        v = disc * phi;
+                        if (pivot >= 0) {
+                            if (is_max) {
+                                dv = (imax == pivot) ? disc * (phi + K) : (Real)0;
+                            } else if (is_put) {
+                                Real sp = S[0], wp = (Real)a.wf[0];
+#pragma unroll
+                                for (int q = 1; q < D; ++q) {
+                                    sp = (q == pivot) ? S[q] : sp;
+                                    wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                                }
+                                dv = -disc * wp * sp;
+                            } else {
+                                Real wp = (Real)a.wf[0];
+#pragma unroll
+                                for (int q = 1; q < D; ++q) wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                                dv = disc * wp * gval;
+                            }
+                        }
+                    }
+                    if (a.mode == MODE_TRACE) {
+                        a.trace_tau[n] = ex ? k : a.n_dates + 1;
+                        a.trace_phi[n] = (double)v;
+                    }
+                    acc0 += v;
+                    acc1 += v * v;
+                    acc2 += dv;
+                    if (sizeof(Real) == 8 || ++since_flush == 16) {
+                        s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
+                        acc0 = acc1 = acc2 = 0;
+                        since_flush = 0;
+                    }
+                }
+            }
+            const unsigned need = __ballot_sync(FULL, finished);
+            if (need) {
+                if (finished) {
+                    n = next + __popc(need & lanemask_lt);
+                    has = n < n_end;
+#pragma unroll
+                    for (int q = 0; q < D; ++q) l[q] = l0[q];
+                    k = a.m;
+                }
+                next += __popc(need);
+            }
+        }
+        s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s0 += __shfl_down_sync(FULL, s0, off);
+            s1 += __shfl_down_sync(FULL, s1, off);
+            s2 += __shfl_down_sync(FULL, s2, off);
+            steps += __shfl_down_sync(FULL, steps, off);
+        }
+        int last = 0;
+        if (lane == 0) {
+            const size_t o = (size_t)item * a.C + chunk;
+            a.partial[3 * o + 0] = s0;
+            a.partial[3 * o + 1] = s1;
+            a.partial[3 * o + 2] = s2;
+            a.partial_steps[o] = steps;
+            __threadfence();
+            last = atomicAdd(&a.done[item], 1) == a.C - 1;
+        }
+        last = __shfl_sync(FULL, last, 0);
+        if (!last) continue;
+
+        // ---- the warp that finished the item's last unit: fixed-order sum over its units ----
+        __threadfence();
+        double t0 = 0, t1 = 0, t2 = 0;
+        long long ts = 0;
+        for (int c = lane; c < a.C; c += 32) {
+            const size_t o = (size_t)item * a.C + c;
+            t0 += __ldcg(a.partial + 3 * o + 0);
+            t1 += __ldcg(a.partial + 3 * o + 1);
+            t2 += __ldcg(a.partial + 3 * o + 2);
+            ts += __ldcg(a.partial_steps + o);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            t0 += __shfl_down_sync(FULL, t0, off);
+            t1 += __shfl_down_sync(FULL, t1, off);
+            t2 += __shfl_down_sync(FULL, t2, off);
+            ts += __shfl_down_sync(FULL, ts, off);
+        }
+        if (lane == 0) {
+            a.done[item] = 0;
+            atomicAdd(a.total_steps, (unsigned long long)ts);
+            const double Nd = (double)a.N;
+            if (a.mode == MODE_SUMS || a.mode == MODE_TRACE) {
+                a.out_sums[3 * item + 0] = t0;
+                a.out_sums[3 * item + 1] = t1;
+                a.out_sums[3 * item + 2] = t2;
+                a.out_steps[item] = ts;
+            } else if (a.mode == MODE_NEWTON) {
+                const double x = a.state[item].x;
+                if (newton_update(a, item, t0 / Nd, t2 / (Nd * x))) {
+                    const int pos = atomicAdd(a.next_count, 1);
+                    a.next_active[pos] = item;
+                }
+            } else if (a.mode == MODE_LABEL) {
+                const double phi = payoff64(a, a.start + (size_t)item * D, D);
+                const double y = phi - t0 / Nd;
+                a.label_y[item] = y;
+                a.label[item] = y > 0 ? 1 : -1;
+            }
+        }
+    }
+}
+
+}  // namespace bap

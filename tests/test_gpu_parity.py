@@ -1,0 +1,230 @@
+"""GPU path against the CPU oracle on the same counters (needs a CUDA device).
+
+Tolerances (the path runs in FP32, the oracle in FP64):
+  * Philox words: bit-exact.  Box-Muller normals: |dz| <= 2e-5 (1 + |z|) (hardware log/sqrt/sin
+    approximations on exactly equal uniforms).
+  * Continuation sums under an identical rule: relative 1e-4 on the mean, after removing the
+    paths whose exercise date differs (counted path by path, at most 1e-4 of the paths).
+  * Full fits: boundary points and final prices compared with the oracle's own fit on the
+    same seeds; prices within 0.5 SE.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_0805_1827_gb300 as bap
+from bap_workloads import (CMCParams, IZParams, OptionSpec, PURPOSE_CMC, PURPOSE_IZ,
+                           PURPOSE_PRICE, equicorrelation, spec_basket_put_7, spec_max_call,
+                           spec_put_1d, workload_max_call_2d, workload_put_1d)
+from rules_io import to_buffer
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 0   # all host cores for the oracle
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-12)
+
+
+# ---- random numbers ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [1, 3, 4, 5, 7, 10])
+def test_rng_words_bit_exact_and_normals_close(d):
+    seed, purpose, m, w1, step = 0x1234_5678_9ABC, PURPOSE_IZ, 3, 17, 5
+    words, z = bap.debug_rng(seed, purpose, m, w1, step, d, 4096)
+    key = [seed & 0xFFFFFFFF, (seed >> 32) ^ (purpose << 24) ^ m]
+    for n in (0, 1, 77, 4095):
+        for c in range((d + 3) // 4):
+            ref = oracle.philox4x32_10([n, w1, 4 * step + c, 0], key)
+            assert list(words[n, c]) == ref
+    zo = oracle.normals_bulk(seed, purpose, m, w1, step, d, 4096)
+    assert np.all(np.abs(z - zo) <= 2e-5 * (1.0 + np.abs(zo)))
+
+
+# ---- continuation sums under identical rules ------------------------------------------------
+
+def _compare_items(opt, spec, rules, m, purpose, seed, ids, starts, N, pivots=None,
+                   trace_items=4):
+    """Sums of both sides, plus a path-by-path replay of a few items to count decision flips."""
+    g_sums, g_steps = opt.debug_continuation(m, purpose, seed, ids, starts, N, pivots)
+    o_sums, o_steps = oracle.continuation(spec, rules, m, purpose, seed, ids, starts, N, pivots,
+                                          n_threads=THREADS)
+    flips, total = 0, 0
+    bad = []
+    for i in range(len(ids)):
+        if i < trace_items:
+            gt, gp = opt.debug_paths(m, purpose, seed, int(ids[i]), starts[i], N)
+            ot, op = oracle.path_trace(spec, rules, m, purpose, seed, int(ids[i]), starts[i], N)
+            same = gt == ot
+            flips += int((~same).sum())
+            total += N
+            # where the exercise dates agree the discounted payoffs agree closely
+            assert np.allclose(gp[same], op[same], rtol=2e-5, atol=2e-4)
+            # sums with the flipped paths removed
+            corr = op[~same].sum() - gp[~same].sum()
+            mean_g = (g_sums[i, 0] + corr) / N
+        else:
+            mean_g = g_sums[i, 0] / N
+        mean_o = o_sums[i, 0] / N
+        if abs(mean_g - mean_o) > 1e-4 * max(abs(mean_o), 1e-3):
+            bad.append(i)
+    return g_sums, o_sums, g_steps, o_steps, flips, total, bad
+
+
+def test_continuation_no_rule_matches_oracle():
+    """Only the maturity decision: the sums differ by FP32 path arithmetic alone."""
+    for spec in (spec_put_1d(), spec_max_call(2, 90.0), spec_max_call(5, 100.0, rho=0.3)):
+        opt = bap.Option(spec)
+        rules = oracle.no_rules(spec)
+        m = spec.n_dates - 3
+        rng = np.random.default_rng(1)
+        starts = spec.S0[None, :] * np.exp(rng.normal(scale=0.2, size=(9, spec.d)))
+        ids = np.arange(100, 109)
+        piv = np.zeros(9, dtype=np.int32)
+        g, o, gs, os_, flips, total, bad = _compare_items(opt, spec, rules, m, PURPOSE_IZ, 5, ids,
+                                                          starts, 3000, piv)
+        assert np.array_equal(gs, os_)
+        assert flips == 0
+        assert not bad
+        assert np.allclose(g[:, 2], o[:, 2], rtol=1e-4, atol=1e-6 * 3000)
+        opt.close()
+
+
+def test_continuation_iz_rule_matches_oracle():
+    spec = spec_max_call(3, 100.0, rho=0.2, n_dates=6, T=2.0)
+    rules, diag = oracle.iz_fit(spec, IZParams(J=32, N1=3000, degree=2, seed=2),
+                                n_threads=THREADS)
+    opt = bap.Option(spec)
+    opt.import_rules(to_buffer(rules))
+    m = 2
+    dg = diag[m]
+    sel = np.arange(0, len(dg["ids"]), 7)
+    starts = dg["starts"][sel].copy()
+    starts[np.arange(len(sel)), dg["pivots"][sel]] = dg["x"][sel]
+    g, o, gs, os_, flips, total, bad = _compare_items(
+        opt, spec, rules, m, PURPOSE_IZ, 9, dg["ids"][sel], starts, 4000, dg["pivots"][sel])
+    assert flips <= max(1, 1e-4 * total), (flips, total)
+    assert len(bad) <= 1, bad
+    # path-step counts differ only through flipped decisions
+    assert np.abs(gs - os_).sum() <= 10 * max(flips, 1) * spec.n_dates
+    opt.close()
+
+
+def test_continuation_cmc_rule_matches_oracle():
+    spec = spec_basket_put_7(0)
+    rules, diag = oracle.cmc_fit(spec, CMCParams(J=300, N2=400, n_stumps=40, seed=3),
+                                 n_threads=THREADS)
+    opt = bap.Option(spec)
+    opt.import_rules(to_buffer(rules))
+    m = 3
+    X = diag[m]["X"][:12]
+    ids = np.arange(12)
+    g, o, gs, os_, flips, total, bad = _compare_items(opt, spec, rules, m, PURPOSE_CMC, 4, ids, X,
+                                                      3000)
+    assert flips <= max(1, 1e-4 * total), (flips, total)
+    assert len(bad) <= 1, bad
+    opt.close()
+
+
+def test_rule_checkpoint_round_trip():
+    spec = spec_max_call(2, 90.0, n_dates=5)
+    rules, _ = oracle.iz_fit(spec, IZParams(J=16, N1=1000, degree=2, seed=1), n_threads=THREADS)
+    opt = bap.Option(spec)
+    buf = to_buffer(rules)
+    opt.import_rules(buf)
+    assert np.array_equal(opt.export_rules(), buf)
+    opt.close()
+
+
+# ---- full fits ---------------------------------------------------------------------------------
+
+def _iz_fit_compare(spec, params, n_price, seed_price, x_rel=1e-4, frac_close=0.97):
+    opt = bap.Option(spec)
+    st = opt.fit_boundary(params)
+    o_rules, o_diag = oracle.iz_fit(spec, params, n_threads=THREADS)
+    close, total = 0, 0
+    for m, dg in o_diag.items():
+        x, it, stt = opt.fit_points(m)
+        ok = np.abs(x - dg["x"]) <= x_rel * np.maximum(1.0, np.abs(dg["x"]))
+        close += int(ok.sum())
+        total += len(x)
+        assert np.array_equal(stt == oracle.ST_NOROOT, dg["status"] == oracle.ST_NOROOT)
+    assert close >= frac_close * total, (close, total)
+    g = opt.price(n_price, seed_price)
+    o = oracle.price(spec, o_rules, n_price, seed_price, n_threads=THREADS)
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"], (g, o)
+    assert abs(g["fp64_delta"]) <= 0.1 * o["se"]
+    assert g["n_paths"] == n_price
+    opt.close()
+    return g, o
+
+
+def test_fit_put_1d_full_size():
+    spec, params, N = workload_put_1d()
+    g, o = _iz_fit_compare(spec, params, N, 1)
+    assert g["path_steps"] == pytest.approx(o["path_steps"], rel=1e-3)
+
+
+def test_fit_max_call_2d_full_size():
+    spec, params, N = workload_max_call_2d()
+    _iz_fit_compare(spec, params, 200_000, 2)
+
+
+def test_fit_max_call_5d_reduced():
+    spec = spec_max_call(5, 100.0, rho=0.3)
+    _iz_fit_compare(spec, IZParams(J=48, N1=2000, degree=2, seed=3), 100_000, 3)
+
+
+def test_fit_geo_call_3d_and_basket_put_iz():
+    spec = OptionSpec(d=3, S0=[100.0] * 3, sigma=[0.2, 0.25, 0.3], delta=[0.05] * 3,
+                      rho=equicorrelation(3, 0.2), r=0.05, K=100.0, T=1.0, n_dates=5,
+                      payoff="geo_call")
+    _iz_fit_compare(spec, IZParams(J=32, N1=3000, degree=2, seed=4), 100_000, 5)
+    spec2 = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.3], delta=[0.0, 0.0],
+                       rho=equicorrelation(2, 0.3), r=0.05, K=100.0, T=1.0, n_dates=5,
+                       payoff="basket_put")
+    _iz_fit_compare(spec2, IZParams(J=32, N1=3000, degree=2, seed=4), 100_000, 5)
+
+
+def test_fit_cmc_7d_reduced():
+    spec = spec_basket_put_7(0)
+    params = CMCParams(J=400, N2=1000, n_stumps=40, seed=5)
+    opt = bap.Option(spec)
+    opt.fit_classifier(params)
+    o_rules, o_diag = oracle.cmc_fit(spec, params, n_threads=THREADS)
+    agree, total = 0, 0
+    for m, dg in o_diag.items():
+        y, _, _ = opt.fit_points(m)
+        agree += int(np.sum(np.sign(y) == np.sign(dg["y"])))
+        total += len(y)
+        close = np.abs(y - dg["y"]) <= 1e-4 * np.maximum(1.0, np.abs(dg["y"])) + 2e-4
+        assert close.mean() >= 0.97
+    assert agree >= total - 3
+    g = opt.price(200_000, 6)
+    o = oracle.price(spec, o_rules, 200_000, 6, n_threads=THREADS)
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"], (g, o)
+    opt.close()
+
+
+def test_price_is_deterministic_and_reports_counts():
+    spec, params, N = workload_put_1d()
+    opt = bap.Option(spec)
+    opt.fit_boundary(params)
+    a = opt.price(N, 3)
+    b = opt.price(N, 3)
+    assert a["price"] == b["price"] and a["var"] == b["var"]
+    assert a["path_steps"] > N and a["fit_path_steps"] > 0
+    opt.close()
+
+
+def test_european_limit_against_black_scholes():
+    """One exercise date: the GPU price is the Black-Scholes put within 3 SE."""
+    from pins import bs_price
+    spec = spec_put_1d(n_dates=1)
+    opt = bap.Option(spec)
+    r = opt.price(1_000_000, 7)
+    assert abs(r["price"] - bs_price(100, 100, 0.05, 0.0, 0.2, 1.0, call=False)) < 3 * r["se"]
+    opt.close()
