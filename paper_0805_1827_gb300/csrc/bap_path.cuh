@@ -468,9 +468,12 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
             atomicAdd(a.total_steps, (unsigned long long)ts);
             const double Nd = (double)a.N;
             if (a.mode == MODE_SUMS || a.mode == MODE_TRACE) {
+                // the pathwise derivative is with respect to the pivot's start value x
+                const int pv = a.pivot ? a.pivot[item] : -1;
+                const double xs = pv >= 0 ? a.start[(size_t)item * D + pv] : 1.0;
                 a.out_sums[3 * item + 0] = t0;
                 a.out_sums[3 * item + 1] = t1;
-                a.out_sums[3 * item + 2] = t2;
+                a.out_sums[3 * item + 2] = t2 / xs;
                 a.out_steps[item] = ts;
             } else if (a.mode == MODE_NEWTON) {
                 const double x = a.state[item].x;

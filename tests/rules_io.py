@@ -8,7 +8,7 @@ import oracle
 def to_buffer(rules: "oracle.Rules") -> np.ndarray:
     nd = rules.n_dates + 1
     head = [rules.kind, rules.n_dates, rules.n_bnd, rules.degree, rules.n_coef,
-            max(1, rules.max_stumps)]
+            rules.max_stumps if rules.kind == oracle.RULE_CMC else 0]
     fitted = list(np.asarray(rules.fitted, dtype=float))
     if rules.kind == oracle.RULE_IZ:
         body = list(np.asarray(rules.coef, dtype=float).ravel())

@@ -141,18 +141,31 @@ def test_rule_checkpoint_round_trip():
 
 # ---- full fits ---------------------------------------------------------------------------------
 
-def _iz_fit_compare(spec, params, n_price, seed_price, x_rel=1e-4, frac_close=0.97):
+def _iz_fit_compare(spec, params, n_price, seed_price):
+    """Boundary points of the device fit against the oracle's own fit.
+
+    At the last fitted date both sides stop paths under the same rule (maturity only), so the
+    points agree to FP32 rounding: relative 1e-5.  At earlier dates each side uses its own
+    fitted later boundaries; a path whose decision flips between the two changes C by one
+    discounted payoff / N1 and moves the point by about that / |f'|, which can be large where
+    f is flat.  So: at least 75% of each date's points within 1e-3 (relative), every point
+    within 5% (a gross-error check), and at least 80% of all points within 1e-4 (no flip)."""
     opt = bap.Option(spec)
-    st = opt.fit_boundary(params)
+    opt.fit_boundary(params)
     o_rules, o_diag = oracle.iz_fit(spec, params, n_threads=THREADS)
+    last = max(o_diag)
     close, total = 0, 0
     for m, dg in o_diag.items():
         x, it, stt = opt.fit_points(m)
-        ok = np.abs(x - dg["x"]) <= x_rel * np.maximum(1.0, np.abs(dg["x"]))
-        close += int(ok.sum())
+        rel = np.abs(x - dg["x"]) / np.maximum(1.0, np.abs(dg["x"]))
+        if m == last:
+            assert np.all(rel <= 1e-5), (m, rel.max())
+        assert np.mean(rel <= 1e-3) >= 0.75, (m, np.sort(rel)[-5:])
+        assert np.all(rel <= 5e-2), (m, rel.max())
+        close += int(np.sum(rel <= 1e-4))
         total += len(x)
         assert np.array_equal(stt == oracle.ST_NOROOT, dg["status"] == oracle.ST_NOROOT)
-    assert close >= frac_close * total, (close, total)
+    assert close >= 0.8 * total, (close, total)
     g = opt.price(n_price, seed_price)
     o = oracle.price(spec, o_rules, n_price, seed_price, n_threads=THREADS)
     assert abs(g["price"] - o["price"]) <= 0.5 * o["se"], (g, o)
@@ -182,11 +195,11 @@ def test_fit_geo_call_3d_and_basket_put_iz():
     spec = OptionSpec(d=3, S0=[100.0] * 3, sigma=[0.2, 0.25, 0.3], delta=[0.05] * 3,
                       rho=equicorrelation(3, 0.2), r=0.05, K=100.0, T=1.0, n_dates=5,
                       payoff="geo_call")
-    _iz_fit_compare(spec, IZParams(J=32, N1=3000, degree=2, seed=4), 100_000, 5)
+    _iz_fit_compare(spec, IZParams(J=32, N1=10_000, degree=2, seed=4), 100_000, 5)
     spec2 = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.3], delta=[0.0, 0.0],
                        rho=equicorrelation(2, 0.3), r=0.05, K=100.0, T=1.0, n_dates=5,
                        payoff="basket_put")
-    _iz_fit_compare(spec2, IZParams(J=32, N1=3000, degree=2, seed=4), 100_000, 5)
+    _iz_fit_compare(spec2, IZParams(J=32, N1=10_000, degree=2, seed=4), 100_000, 5)
 
 
 def test_fit_cmc_7d_reduced():
