@@ -176,6 +176,28 @@ bap_status bap_debug_continuation(bap_option *opt, int m, int purpose, uint64_t 
 bap_status bap_debug_paths(bap_option *opt, int m, int purpose, uint64_t seed, int item_id,
                            const double *start, int64_t N, int *tau, double *disc_phi);
 
+/* Continuation sums that allocate no device memory.  The paper has no counterpart to this call.
+ * It is for callers that cannot allocate device memory while they run -- code inside a host
+ * framework whose allocator owns all of the GPU's memory, or a latency-bound loop that must not
+ * call cudaMalloc or cudaFree (both can block on the whole device) -- and that bring their own
+ * device buffers.  It computes what bap_debug_continuation computes, but:
+ *   - every array is a DEVICE pointer: d_item_ids and d_pivots (n_items ints; d_pivots may be
+ *     NULL), d_starts (n_items*d doubles), d_sums (n_items*3 doubles), d_steps (n_items);
+ *   - the call only enqueues work on the option's stream and returns; synchronize that stream
+ *     before reading d_sums and d_steps;
+ *   - its scratch is a fixed 4 MiB array in the library's device image (one per GPU that loads
+ *     the library, held until the process exits).  A call needs about 32 bytes per
+ *     (item, unit of up to 2048 paths) plus 4 bytes per item; larger calls return BAP_EINVAL;
+ *   - the first call on a device looks up the array's address (that device must be current, as
+ *     for every call on the option); make that first call before any stream capture;
+ *   - all calls share the array, and it keeps the last call's contents (the call clears what it
+ *     needs zeroed): calls whose work overlaps on the GPU -- on different streams, or different
+ *     options on one device -- race on it and corrupt each other's sums.  Serialize them. */
+bap_status bap_continuation_static(bap_option *opt, int m, int purpose, uint64_t seed,
+                                   int n_items, const int *d_item_ids, const int *d_pivots,
+                                   const double *d_starts, int64_t N, double *d_sums,
+                                   int64_t *d_steps);
+
 /* Raw Philox4x32-10 words and the Box-Muller normals of the counters (n, w1, 4*step + c),
  * n = 0..count-1, under key (seed, purpose, m) (parity hook; no option needed).  words:
  * count * 4 * ceil(d/4) uint32 (may be NULL); z: count * d doubles converted from the FP32

@@ -948,3 +948,126 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Continuation sums for callers that cannot allocate device memory.
+//
+// The scratch of the path kernel (per-unit partial sums, per-item unit counters, the work
+// counter, the item count and the step total) lives in one fixed array in this library's device
+// image instead of in buffers from cudaMalloc.  Every GPU that loads the library holds the array
+// until the process exits.  Host code never names the array as an address: the first call on a
+// device looks its address up with cudaGetSymbolAddress (with that device current) and caches
+// it.  All calls share the array and it keeps the last call's contents, so the call clears what
+// must start at zero; calls whose work overlaps on the GPU race on it.
+
+#define BAP_STATIC_SCRATCH_BYTES (4u << 20)
+
+static __device__ __align__(256) unsigned char bap_static_scratch[BAP_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_base[kMaxStaticDevices] = {nullptr};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// Header of the array: [0] work counter (u64), [8] step total (u64), [16] item count (int).
+__global__ void static_scratch_clear_kernel(unsigned char* base, int n_items, size_t done_off) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *reinterpret_cast<unsigned long long*>(base) = 0ULL;
+        *reinterpret_cast<unsigned long long*>(base + 8) = 0ULL;
+        *reinterpret_cast<int*>(base + 16) = n_items;
+    }
+    int* done = reinterpret_cast<int*>(base + done_off);
+    for (int k = i; k < n_items; k += gridDim.x * blockDim.x) done[k] = 0;
+}
+
+}  // namespace
+
+extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose, uint64_t seed,
+                                              int n_items, const int* d_item_ids,
+                                              const int* d_pivots, const double* d_starts,
+                                              int64_t N, double* d_sums, int64_t* d_steps) {
+    g_err.clear();
+    if (!o || !d_item_ids || !d_starts || !d_sums || !d_steps) return fail(BAP_EINVAL, "null argument");
+    if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
+    if (n_items < 1 || N < 1 || N > (1LL << 31)) return fail(BAP_EINVAL, "bad n_items or N");
+    if (purpose < 1 || purpose > 4) return fail(BAP_EINVAL, "bad purpose");
+    const int chunk = choose_chunk(n_items, N);
+    const long long C = (N + chunk - 1) / chunk;
+    const long long units = (long long)n_items * C;
+    const size_t done_off = 256;
+    const size_t steps_off = done_off + align256((size_t)n_items * 4);
+    const size_t partial_off = steps_off + align256((size_t)units * 8);
+    const size_t need = partial_off + (size_t)units * 24;
+    if (need > BAP_STATIC_SCRATCH_BYTES)
+        return fail(BAP_EINVAL,
+                    "n_items=%d with N=%lld needs %zu bytes of scratch; the static scratch holds %u "
+                    "bytes (use bap_debug_continuation, which allocates)",
+                    n_items, (long long)N, need, (unsigned)BAP_STATIC_SCRATCH_BYTES);
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != o->device) return fail(BAP_EINVAL, "the option's device %d is not current (%d)", o->device, dev);
+    if (dev < 0 || dev >= kMaxStaticDevices) return fail(BAP_EINVAL, "device %d out of range", dev);
+    unsigned char* base;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_base[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, bap_static_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(BAP_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+            g_static_base[dev] = static_cast<unsigned char*>(p);
+        }
+        base = g_static_base[dev];
+    }
+    static_scratch_clear_kernel<<<std::min(1024, (n_items + 255) / 256), 256, 0, o->stream>>>(base, n_items, done_off);
+    CU(cudaGetLastError());
+
+    PathArgs a;
+    base_args(o, a, m, MODE_SUMS, false);
+    a.rk = make_round_keys(seed, (uint32_t)purpose, (uint32_t)m);
+    a.N = N;
+    a.chunk = chunk;
+    a.C = (int)C;
+    a.active = nullptr;
+    a.n_active = reinterpret_cast<const int*>(base + 16);
+    a.work = reinterpret_cast<unsigned long long*>(base);
+    a.total_steps = reinterpret_cast<unsigned long long*>(base + 8);
+    a.start = const_cast<double*>(d_starts);
+    a.ctr_item = d_item_ids;
+    a.pivot = d_pivots;
+    a.done = reinterpret_cast<int*>(base + done_off);
+    a.partial_steps = reinterpret_cast<long long*>(base + steps_off);
+    a.partial = reinterpret_cast<double*>(base + partial_off);
+    a.out_sums = d_sums;
+    a.out_steps = reinterpret_cast<long long*>(d_steps);
+
+    const int rule = o->rule_kind;
+    const void* fn = path_fn(o->d, rule, false);
+    if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
+    const int nk = a.n_dates - a.m;
+    size_t smem = nk * sizeof(float) * (1 + (a.uniform ? 0 : 2 * o->d));
+    if (rule != R_NONE) smem += (size_t)(nk - 1) * a.rule_stride * sizeof(float);
+    smem = (smem + 7) & ~size_t(7);
+    smem += nk * sizeof(int);
+    if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
+    int bps = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_fn_mu);
+        FnInfo& fi = g_fn[fn];
+        if (smem > fi.smem_set) {
+            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
+            fi.smem_set = std::max<size_t>(smem, 48 * 1024);
+        }
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
+    }
+    if (bps < 1) bps = 1;
+    long long blocks = (units + (kBlock / 32) - 1) / (kBlock / 32);
+    blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
+    void* args[] = {&a};
+    CU(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
+    return BAP_OK;
+}
