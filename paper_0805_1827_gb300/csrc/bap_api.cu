@@ -150,18 +150,20 @@ int choose_chunk(long long n_items, long long N) {
     c = std::min(c, std::max(32LL, nr));
     // very long pricing runs: keep the unit count below 2^24
     while ((N + c - 1) / c > (1LL << 24)) c *= 2;
+    // beyond 2^32 paths the counter's high word must stay fixed inside a unit: a power-of-two
+    // unit never straddles a multiple of 2^32
+    if (N > (1LL << 32)) {
+        long long p2 = 64;
+        while (p2 < c) p2 <<= 1;
+        c = p2;
+    }
     return (int)c;
 }
 
 bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units) {
     const void* fn = path_fn(o->d, rule, fp64);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
-    const int nk = a.n_dates - a.m;
-    const size_t real = fp64 ? 8 : 4;
-    size_t smem = nk * real * (1 + (a.uniform ? 0 : 2 * o->d));
-    if (rule != R_NONE) smem += (size_t)(nk - 1) * a.rule_stride * real;
-    smem = (smem + 7) & ~size_t(7);
-    smem += nk * sizeof(int);
+    const size_t smem = path_smem_bytes(a, rule, fp64, o->d);
     if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps;
     {
@@ -235,9 +237,9 @@ void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
     a.fitted = o->fitted.as<int>();
     if (o->rule_kind == R_IZ) {
         a.rule_src = fp64 ? (const void*)o->coef_d.p : (const void*)o->coef_f.p;
-        a.rule_stride = o->n_bnd * o->n_coef;
+        a.rule_stride = o->n_bnd * iz_stage_stride(o->d);
         a.n_bnd = o->n_bnd;
-        a.n_coef = o->n_coef;
+        a.n_coef = iz_stage_stride(o->d);
         a.degree = o->degree;
     } else if (o->rule_kind == R_CMC) {
         a.rule_src = fp64 ? (const void*)o->rec_d.p : (const void*)o->rec_f.p;
@@ -253,12 +255,13 @@ bap_status set_rule_iz(bap_option* o, int degree) {
     o->degree = degree;
     o->n_coef = n_basis(s, degree);
     const size_t nc = (size_t)(o->n_dates + 1) * o->n_bnd * o->n_coef;
+    const size_t ns = (size_t)(o->n_dates + 1) * o->n_bnd * iz_stage_stride(o->d);
     TRY(o->coef64.reserve(nc * 8));
-    TRY(o->coef_f.reserve(nc * 4));
-    TRY(o->coef_d.reserve(nc * 8));
+    TRY(o->coef_f.reserve(ns * 4));
+    TRY(o->coef_d.reserve(ns * 8));
     CU(cudaMemsetAsync(o->coef64.p, 0, nc * 8, o->stream));
-    CU(cudaMemsetAsync(o->coef_f.p, 0, nc * 4, o->stream));
-    CU(cudaMemsetAsync(o->coef_d.p, 0, nc * 8, o->stream));
+    CU(cudaMemsetAsync(o->coef_f.p, 0, ns * 4, o->stream));
+    CU(cudaMemsetAsync(o->coef_d.p, 0, ns * 8, o->stream));
     CU(cudaMemsetAsync(o->fitted.p, 0, (o->n_dates + 1) * sizeof(int), o->stream));
     return BAP_OK;
 }
@@ -1048,11 +1051,7 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     const int rule = o->rule_kind;
     const void* fn = path_fn(o->d, rule, false);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
-    const int nk = a.n_dates - a.m;
-    size_t smem = nk * sizeof(float) * (1 + (a.uniform ? 0 : 2 * o->d));
-    if (rule != R_NONE) smem += (size_t)(nk - 1) * a.rule_stride * sizeof(float);
-    smem = (smem + 7) & ~size_t(7);
-    smem += nk * sizeof(int);
+    const size_t smem = path_smem_bytes(a, rule, false, o->d);
     if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps = 1;
     {

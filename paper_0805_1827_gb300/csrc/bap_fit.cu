@@ -191,28 +191,26 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
 
 // ---------------------------------------------------------------------------------------------
 // Staging of an I&Z boundary (date m, boundary b) for the path kernel: coefficients of
-// x/K = B(y/K) in [1, y_a, y_a y_b (a<=b)] order become the Horner layout
-// [K c_0, for a: c_a, c_ab / K (b = a..s-1)] of B''(S) = K B(S/K) in price units.
+// x/K = B(y/K) in [1, y_a, y_a y_b (a<=b)] order (for the given degree) become the full
+// quadratic Horner layout [K c_0, for a: c_a, c_ab / K (b = a..s-1)] of B''(S) = K B(S/K) in
+// price units, zero-filled for lower degrees and padded to iz_stage_stride(s + 1) values.
 
 __device__ void stage_iz_one(const double* c, int s, int degree, double K, float* out_f,
                              double* out_d) {
+    const int stride = iz_stage_stride(s + 1);
+    for (int i = 0; i < stride; ++i) { out_f[i] = 0.f; out_d[i] = 0.0; }
     out_f[0] = (float)(K * c[0]);
     out_d[0] = K * c[0];
-    if (degree == 1) {
-        for (int t = 0; t < s; ++t) {
-            out_f[1 + t] = (float)c[1 + t];
-            out_d[1 + t] = c[1 + t];
-        }
-    } else if (degree == 2) {
-        int o = 1, qidx = 1 + s;
-        for (int t = 0; t < s; ++t) {
-            out_f[o] = (float)c[1 + t];
-            out_d[o] = c[1 + t];
-            ++o;
-            for (int u = t; u < s; ++u, ++qidx, ++o) {
-                out_f[o] = (float)(c[qidx] / K);
-                out_d[o] = c[qidx] / K;
-            }
+    int o = 1, qidx = 1 + s;
+    for (int t = 0; t < s; ++t) {
+        const double lin = degree >= 1 ? c[1 + t] : 0.0;
+        out_f[o] = (float)lin;
+        out_d[o] = lin;
+        ++o;
+        for (int u = t; u < s; ++u, ++o) {
+            const double q = degree >= 2 ? c[qidx++] / K : 0.0;
+            out_f[o] = (float)q;
+            out_d[o] = q;
         }
     }
 }
@@ -221,8 +219,8 @@ __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, in
                                 int degree, double K, float* coef_f, double* coef_d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (n_dates + 1) * n_bnd) return;
-    const size_t o = (size_t)i * n_coef;
-    stage_iz_one(coef64 + o, s, degree, K, coef_f + o, coef_d + o);
+    const size_t so = (size_t)i * iz_stage_stride(s + 1);
+    stage_iz_one(coef64 + (size_t)i * n_coef, s, degree, K, coef_f + so, coef_d + so);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -368,7 +366,8 @@ __global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int de
         }
         const size_t o = ((size_t)m * n_bnd + b) * P;
         for (int i = 0; i < P; ++i) coef64[o + i] = coef[i];
-        stage_iz_one(coef64 + o, s, degree, K, coef_f + o, coef_d + o);
+        const size_t so = ((size_t)m * n_bnd + b) * iz_stage_stride(d);
+        stage_iz_one(coef64 + o, s, degree, K, coef_f + so, coef_d + so);
         if (b == 0) fitted[m] = 1;
     }
 }

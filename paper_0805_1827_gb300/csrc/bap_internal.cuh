@@ -60,12 +60,21 @@ __host__ __device__ inline RoundKeys make_round_keys(uint64_t seed, uint32_t pur
     return rk;
 }
 
+// 32 x 32 -> 64-bit product in one instruction (both halves of the Philox multiply).
+__device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    uint64_t p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         const RoundKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        uint32_t lo0, hi0, lo1, hi1;
+        mulhilo(0xD2511F53u, c0, hi0, lo0);
+        mulhilo(0xCD9E8D57u, c2, hi1, lo1);
         uint32_t n0 = hi1 ^ c1 ^ rk.k0[r];
         uint32_t n2 = hi0 ^ c3 ^ rk.k1[r];
         c0 = n0;
@@ -155,6 +164,13 @@ __host__ __device__ inline int n_basis(int s, int degree) {
     if (degree >= 1) n += s;
     if (degree >= 2) n += s * (s + 1) / 2;
     return n;
+}
+
+// Staged I&Z boundary block for the path kernel: always the full quadratic in the d-1 other
+// assets (lower degrees carry zero coefficients), padded to a multiple of 4 values so that a
+// block is read with 16-byte vector loads.
+__host__ __device__ constexpr int iz_stage_stride(int d) {
+    return ((1 + (d - 1) + (d - 1) * d / 2) + 3) & ~3;
 }
 
 // CMC staged rule record per date (floats or doubles; counts and offsets stored as values):

@@ -179,20 +179,59 @@ __device__ inline bool newton_update(const PathArgs& a, int item, double C, doub
 
 // ---------------------------------------------------------------------------------------------
 
+// Resident 256-thread blocks per SM the register budget is sized for (no spills at these).
+template <int D, typename Real> constexpr int path_min_blocks() {
+    return sizeof(Real) == 8 ? 2 : (D <= 5 ? 4 : (D <= 9 ? 3 : 2));
+}
+
+// Dynamic shared memory of one launch: the staged rules of dates m+1..NT-1 first (16-byte
+// aligned), then the discount factors, the per-date stepping constants (non-uniform dates
+// only) and the per-date "fitted" flags.
+inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
+    const size_t nk = (size_t)(a.n_dates - a.m);
+    const size_t n = (rule != R_NONE ? (nk - 1) * (size_t)a.rule_stride : 0) + nk +
+                     (a.uniform ? 0 : 2 * nk * (size_t)d);
+    return n * (fp64 ? 8 : 4) + nk * sizeof(int);
+}
+
+// Loads N consecutive values from 16-byte-aligned shared memory with vector loads.
+template <int N>
+__device__ __forceinline__ void load_vec(const float* src, float (&dst)[N]) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+        const float4 v = s4[i];
+        dst[4 * i] = v.x; dst[4 * i + 1] = v.y; dst[4 * i + 2] = v.z; dst[4 * i + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void load_vec(const double* src, double (&dst)[N]) {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const double2 v = s2[i];
+        dst[2 * i] = v.x; dst[2 * i + 1] = v.y;
+    }
+}
+
 template <int D, int RULE, typename Real>
-__global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
+__global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NF = D + 1;
+    constexpr int P4 = iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
-    Real* sh_disc = reinterpret_cast<Real*>(smem_raw);
+    const int rule_len = (RULE == R_NONE) ? 0 : (nk - 1) * a.rule_stride;   // dates m+1..NT-1
+    Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
+    Real* sh_disc = sh_rule + rule_len;
     Real* sh_drift = sh_disc + nk;                   // non-uniform dates: [nk][D]
     Real* sh_vol = sh_drift + (a.uniform ? 0 : nk * D);
-    Real* sh_rule = sh_vol + (a.uniform ? 0 : nk * D);
-    const int n_rule_dates = nk - 1;                 // fitted dates m+1..NT-1
-    const int rule_len = (RULE == R_NONE) ? 0 : n_rule_dates * a.rule_stride;
-    int* sh_fit = reinterpret_cast<int*>(sh_rule + rule_len);
+    int* sh_fit = reinterpret_cast<int*>(sh_vol + (a.uniform ? 0 : nk * D));
 
     const DevModel* M = a.model;
+    if (RULE != R_NONE) {
+        const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
+        for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
+    }
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         const int k = a.m + 1 + i;
         sh_disc[i] = (Real)exp(-a.r * (M->t[k] - M->t[a.m]));
@@ -205,10 +244,6 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
             sh_vol[i] = (Real)M->vol2[k][q];
         }
     }
-    if (RULE != R_NONE) {
-        const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
-        for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
-    }
     __syncthreads();
 
     const unsigned FULL = 0xffffffffu;
@@ -218,16 +253,17 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
     const Real K = (Real)a.K;
     const bool is_put = a.payoff == BAP_BASKET_PUT;
     const bool is_max = a.payoff == BAP_MAX_CALL;
-    const bool is_geo = a.payoff == BAP_GEO_CALL;
 
-    Real Lr[D * (D + 1) / 2];
-    Real drift_u[D];
-#pragma unroll
-    for (int q = 0, o = 0; q < D; ++q)
-#pragma unroll
-        for (int j = 0; j <= q; ++j, ++o) Lr[o] = sizeof(Real) == 4 ? (Real)a.Lf[q * MAXD + j] : (Real)a.Ld[q * MAXD + j];
-#pragma unroll
-    for (int q = 0; q < D; ++q) drift_u[q] = sizeof(Real) == 4 ? (Real)a.driftf[q] : (Real)a.driftd[q];
+    // The Cholesky factor and the per-step drift are read straight from the kernel parameters
+    // (constant bank operands, no registers).
+    auto Lc = [&](int q, int j) -> Real {
+        if constexpr (sizeof(Real) == 4) return a.Lf[q * MAXD + j];
+        else return a.Ld[q * MAXD + j];
+    };
+    auto drift_c = [&](int q) -> Real {
+        if constexpr (sizeof(Real) == 4) return a.driftf[q];
+        else return a.driftd[q];
+    };
 
     while (true) {
         unsigned long long unit_u = 0;
@@ -238,51 +274,62 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
         const int chunk = (int)(unit - (long long)slot * a.C);
         const int item = a.active ? a.active[slot] : slot;
 
+        // log2 of the start point in FP64, one coordinate per lane, then broadcast
         const double* st = a.start + (size_t)item * D;
+        const double my_l0 = lane < D ? log2(st[lane]) : 0.0;
         Real l0[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) l0[q] = (Real)log2(st[q]);
-        const uint32_t item_word = a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u;
+        for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
         const int pivot = a.pivot ? a.pivot[item] : -1;
+        // The unit covers paths n_begin .. n_begin + n_count - 1.  Inside the loop only the
+        // 32-bit offset nl moves: counter word 0 is (n_begin + nl) mod 2^32 and word 1 stays
+        // item + n_begin / 2^32 (a unit never straddles a multiple of 2^32 paths).
         const long long n_begin = (long long)chunk * a.chunk;
-        const long long n_end = min((long long)a.N, n_begin + a.chunk);
+        const int n_count = (int)min((long long)a.chunk, (long long)a.N - n_begin);
+        const uint32_t w0_base = (uint32_t)n_begin;
+        const uint32_t w1_word = (a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u) + (uint32_t)(n_begin >> 32);
 
-        long long n = n_begin + lane;
-        bool has = n < n_end;
-        long long next = n_begin + 32;
+        int nl = lane;
+        bool has = nl < n_count;
+        int next = 32;
         Real l[D];
 #pragma unroll
         for (int q = 0; q < D; ++q) l[q] = l0[q];
         int k = a.m;
         Real acc0 = 0, acc1 = 0, acc2 = 0;
         double s0 = 0, s1 = 0, s2 = 0;
-        int since_flush = 0;
-        long long steps = 0;
+        int steps = 0;
 
-        while (__any_sync(FULL, has)) {
+        // Blocks of up to 32 warp steps; the FP32 partial sums move to FP64 after each block
+        // (a lane ends at most 32 paths in between).  The flush sits outside the inner loop on
+        // purpose: inside it the compiler would evaluate it speculatively on every step, and the
+        // FP64 pipe runs at 1/64 of the FP32 rate.
+        bool live = true;
+        while (live) {
+        for (int it = 0; it < 32; ++it) {
+            live = __any_sync(FULL, has);
+            if (!live) break;
             bool finished = false;
             if (has) {
                 k += 1;
                 ++steps;
                 Real z[D];
-                normals<D, Real>((uint32_t)n, item_word + (uint32_t)(n >> 32), (uint32_t)k, a.rk, z);
+                normals<D, Real>(w0_base + (uint32_t)nl, w1_word, (uint32_t)k, a.rk, z);
                 if (a.uniform) {
 #pragma unroll
                     for (int q = 0; q < D; ++q) {
-                        const int o = q * (q + 1) / 2;
                         Real wq = 0;
 #pragma unroll
-                        for (int j = 0; j <= q; ++j) wq = fma(Lr[o + j], z[j], wq);
-                        l[q] = l[q] + drift_u[q] + wq;
+                        for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
+                        l[q] = l[q] + drift_c(q) + wq;
                     }
                 } else {
                     const int kk = (k - a.m - 1) * D;
 #pragma unroll
                     for (int q = 0; q < D; ++q) {
-                        const int o = q * (q + 1) / 2;
                         Real wq = 0;
 #pragma unroll
-                        for (int j = 0; j <= q; ++j) wq = fma(Lr[o + j], z[j], wq);
+                        for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
                         l[q] = fma(sh_vol[kk + q], wq, l[q] + sh_drift[kk + q]);
                     }
                 }
@@ -320,38 +367,35 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
                     if (RULE == R_NONE || !sh_fit[kr]) {
                         ex = false;
                     } else if (RULE == R_IZ) {
+                        // exercise iff S_p passes B''(S_{-p}) (full quadratic, Horner order)
                         const int p = is_max ? imax : 0;
                         Real sp = S[0];
 #pragma unroll
                         for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
-                        const Real* c = sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * a.n_coef;
-                        Real B = c[0];
-                        if (D > 1) {
-                            Real y[D > 1 ? D - 1 : 1];
+                        Real cc[P4];
+                        load_vec<P4>(sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
+                        Real B = cc[0];
+                        if constexpr (D > 1) {
+                            Real y[D - 1];
 #pragma unroll
                             for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
-                            if (a.degree == 2) {
-                                int idx = 1;
+                            int idx = 1;
 #pragma unroll
-                                for (int t = 0; t < D - 1; ++t) {
-                                    Real acc = c[idx++];
+                            for (int t = 0; t < D - 1; ++t) {
+                                Real acc = cc[idx++];
 #pragma unroll
-                                    for (int u = t; u < D - 1; ++u) acc = fma(c[idx++], y[u], acc);
-                                    B = fma(acc, y[t], B);
-                                }
-                            } else if (a.degree == 1) {
-#pragma unroll
-                                for (int t = 0; t < D - 1; ++t) B = fma(c[1 + t], y[t], B);
+                                for (int u = t; u < D - 1; ++u) acc = fma(cc[idx++], y[u], acc);
+                                B = fma(acc, y[t], B);
                             }
                         }
                         ex = is_put ? (sp <= B) : (sp >= B);
-                    } else {  // R_CMC
+                    } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
                         const Real* rec = sh_rule + kr * a.rule_stride;
                         Real F = rec[0];
 #pragma unroll
                         for (int f = 0; f < NF; ++f) {
                             int nf, off;
-                            if (sizeof(Real) == 4) {
+                            if constexpr (sizeof(Real) == 4) {
                                 nf = __float_as_int((float)rec[2 + f]);
                                 off = __float_as_int((float)rec[2 + NF + f]);
                             } else {
@@ -399,24 +443,19 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
                         }
                     }
                     if (a.mode == MODE_TRACE) {
-                        a.trace_tau[n] = ex ? k : a.n_dates + 1;
-                        a.trace_phi[n] = (double)v;
+                        a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
+                        a.trace_phi[n_begin + nl] = (double)v;
                     }
                     acc0 += v;
                     acc1 += v * v;
                     acc2 += dv;
-                    if (sizeof(Real) == 8 || ++since_flush == 16) {
-                        s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
-                        acc0 = acc1 = acc2 = 0;
-                        since_flush = 0;
-                    }
                 }
             }
             const unsigned need = __ballot_sync(FULL, finished);
             if (need) {
                 if (finished) {
-                    n = next + __popc(need & lanemask_lt);
-                    has = n < n_end;
+                    nl = next + __popc(need & lanemask_lt);
+                    has = nl < n_count;
 #pragma unroll
                     for (int q = 0; q < D; ++q) l[q] = l0[q];
                     k = a.m;
@@ -425,12 +464,15 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
             }
         }
         s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
+        acc0 = acc1 = acc2 = 0;
+        }
+        long long steps64 = steps;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             s0 += __shfl_down_sync(FULL, s0, off);
             s1 += __shfl_down_sync(FULL, s1, off);
             s2 += __shfl_down_sync(FULL, s2, off);
-            steps += __shfl_down_sync(FULL, steps, off);
+            steps64 += __shfl_down_sync(FULL, steps64, off);
         }
         int last = 0;
         if (lane == 0) {
@@ -438,7 +480,7 @@ __global__ void __launch_bounds__(256, 2) path_kernel(const PathArgs a) {
             a.partial[3 * o + 0] = s0;
             a.partial[3 * o + 1] = s1;
             a.partial[3 * o + 2] = s2;
-            a.partial_steps[o] = steps;
+            a.partial_steps[o] = steps64;
             __threadfence();
             last = atomicAdd(&a.done[item], 1) == a.C - 1;
         }
