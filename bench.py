@@ -27,7 +27,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from bap_workloads import IZParams, spec_max_call  # noqa: E402
+from bap_workloads import IZParams, serving_stream, spec_max_call  # noqa: E402
 
 S0S = (90.0, 100.0, 110.0)
 J_FULL, N1_FULL, N_PRICE = 1024, 100_000, 1_000_000
@@ -189,6 +189,72 @@ def cpu_baseline() -> dict:
                        f"({steps} path-steps in {el:.1f} s); FP64 C with OpenMP over items")}
 
 
+def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
+    """The mixed request stream (Poisson arrivals, mean 2 ms; d ~ U{1..10}; 4..50 dates; inner
+    budget log-uniform 1e4..1e6; mixed payoffs; I&Z or CMC) replayed in real time through the
+    server, then through the plain per-request form: the same direct calls one request at a
+    time, one launch per Newton pass.  Latency = completion - arrival on the host clock."""
+    reqs = serving_stream(n=n_req, seed=0)
+
+    def summary(lat, span):
+        lat = sorted(lat)
+        return {"options_per_s": len(lat) / span, "p50_ms": 1e3 * lat[len(lat) // 2],
+                "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "makespan_s": span}
+
+    srv = bap.Server(budget, max_inflight)
+    t0 = time.perf_counter()
+    pending, served, lat = {}, {}, {}
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].arrival_s <= now:
+            r = reqs[i]
+            pending[srv.submit(r.spec, r.params, r.n_paths, r.seed)] = i
+            i += 1
+        done = []
+        for t, j in pending.items():
+            out = srv.poll(t)
+            if out is not None:
+                served[j] = out[1]
+                lat[j] = time.perf_counter() - t0 - reqs[j].arrival_s
+                done.append(t)
+        for t in done:
+            del pending[t]
+        if not done:
+            time.sleep(0.0002)
+    span_srv = time.perf_counter() - t0 - reqs[0].arrival_s
+    stats = srv.stats()
+    srv.close()
+
+    t0 = time.perf_counter()
+    plain, lat_p = {}, {}
+    for j, r in enumerate(reqs):
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        o = bap.Option(r.spec)
+        o.set_launch_mode(bap.LAUNCH_PLAIN)
+        if r.method == "iz":
+            o.fit_boundary(r.params)
+        else:
+            o.fit_classifier(r.params)
+        plain[j] = o.price(r.n_paths, r.seed)
+        o.close()
+        lat_p[j] = time.perf_counter() - t0 - r.arrival_s
+    span_plain = time.perf_counter() - t0 - reqs[0].arrival_s
+    mismatches = sum(1 for j in range(len(reqs)) if served[j]["price"] != plain[j]["price"])
+    steps = sum(v["fit_path_steps"] + v["path_steps"] for v in served.values())
+    return {"workload": f"{len(reqs)} requests, Poisson arrivals (mean 2 ms), d~U{{1..10}}, "
+                        "4..50 dates, inner budget log-U[1e4,1e6], mixed payoffs, I&Z/CMC 50/50, "
+                        "pricing 1e5 paths",
+            "served": {**summary(list(lat.values()), span_srv), "max_inflight": max_inflight,
+                       "peak_inflight": stats["peak_inflight"]},
+            "plain_per_request": summary(list(lat_p.values()), span_plain),
+            "results_equal": mismatches == 0, "mismatches": mismatches,
+            "path_steps": steps}
+
+
 def run_ours(args) -> None:
     import torch
     import paper_0805_1827_gb300 as bap
@@ -321,6 +387,8 @@ def run_ours(args) -> None:
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},
     }
+    if args.serving > 0:
+        line["serving"] = serving_bench(bap, args.serving, args.max_inflight, 64 << 30)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -335,6 +403,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=512,
+                    help="requests in the served-stream measurement (0: skip)")
+    ap.add_argument("--max-inflight", type=int, default=32)
     ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
     ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
     args = ap.parse_args()

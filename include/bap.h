@@ -120,7 +120,16 @@ typedef struct bap_result {
     double path_kernel_ms;    /* summed CUDA-event time of those path-kernel launches (only with
                                  bap_set_profiling on; else 0); the FP64 check of
                                  bap_price is not timed */
+    double queue_ms;          /* served requests: submit -> admission (host clock) */
+    double latency_ms;        /* served requests: submit -> completion (host clock) */
 } bap_result;
+
+typedef struct bap_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t queued;           /* waiting for admission now */
+    int64_t bytes_in_use;     /* estimated device memory of the requests in flight now */
+    int64_t peak_bytes, peak_inflight;
+} bap_server_stats;
 
 typedef struct bap_option bap_option;
 typedef struct bap_server bap_server;
@@ -135,6 +144,14 @@ bap_status bap_set_stream(bap_option *opt, void *cuda_stream);
 /* 1: time every path-kernel launch with a CUDA event pair on the option's stream (reported in
  * bap_result.path_kernel_ms); 0 (default): no per-launch events. */
 bap_status bap_set_profiling(bap_option *opt, int on);
+
+/* How bap_fit_boundary issues its work.  1 (default): the whole fit is one CUDA graph, built on
+ * the first fit of a parameter set and replayed; each date's Newton loop is a conditional while
+ * node whose body runs one Newton pass and then a one-thread kernel that continues the loop only
+ * while points remain unconverged (at most max_iter passes), so the loop costs no host round
+ * trip and no empty launches.  0: plain form, one launch per Newton pass up to max_iter per date
+ * (also used while profiling is on).  If the graph cannot be built, the plain form is used. */
+bap_status bap_set_launch_mode(bap_option *opt, int mode);
 
 /* Ibanez-Zapatero fit (Algorithm 1 without [mc]): for m = N_T-1..1, boundary points by
  * device Newton on N1-path continuation estimates, then an FP64 least-squares boundary per
@@ -204,6 +221,42 @@ bap_status bap_continuation_static(bap_option *opt, int m, int purpose, uint64_t
  * normals (may be NULL). */
 bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_t step, int d,
                          int64_t count, uint32_t *words, double *z);
+
+/* ---- Serving (continuous batching) ----------------------------------------------------------
+ * A server owns a thread that admits submitted requests while the requests in flight number at
+ * most max_inflight and their estimated device memory stays within device_mem_budget bytes.  It
+ * runs each admitted request -- create, fit (I&Z graph or CMC), price -- on a stream of its own,
+ * so requests overlap on the device; when one finishes its slot and memory go to the next in
+ * the queue.  A request's result depends only on its inputs: it is the same, bitwise, as the
+ * same calls made alone through bap_create / bap_fit_* / bap_price.  All server calls are
+ * thread safe.  The server uses the device current at bap_server_create. */
+
+/* Errors: EINVAL (budget < 1 MiB, max_inflight outside 1..1024), ECUDA (no device), ENOMEM. */
+bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_server **out);
+
+/* Launch form of the I&Z fits the server runs (see bap_set_launch_mode; default 1). */
+bap_status bap_server_set_launch_mode(bap_server *srv, int mode);
+
+/* Queue a request: method BAP_METHOD_IZ with params -> bap_iz_params, or BAP_METHOD_CMC with
+ * params -> bap_cmc_params; then pricing with n_paths paths and `seed`.  The model and params
+ * are copied.  *ticket identifies the request.  Errors: EINVAL (bad arguments, checked as
+ * bap_create / bap_fit_* would), EBUSY (the request alone needs more than the budget). */
+bap_status bap_submit(bap_server *srv, const bap_model *model, int method, const void *params,
+                      int64_t n_paths, uint64_t seed, uint64_t *ticket);
+
+/* Non-blocking: BAP_ENOTREADY while queued or running; otherwise the request's final status
+ * (OK, ENOCONV, or its error) with *out filled (may be NULL), after which the ticket is gone.
+ * EINVAL for an unknown ticket. */
+bap_status bap_poll(bap_server *srv, uint64_t ticket, bap_result *out);
+
+/* As bap_poll, but waits up to timeout_s seconds; BAP_ETIMEOUT if still not done. */
+bap_status bap_wait(bap_server *srv, uint64_t ticket, double timeout_s, bap_result *out);
+
+bap_status bap_server_get_stats(bap_server *srv, bap_server_stats *out);
+
+/* Finishes every queued and running request, then stops the thread and frees everything
+ * (results not collected are discarded). NULL is ignored. */
+void bap_server_destroy(bap_server *srv);
 
 /* Release an option and its device memory (NULL is ignored). */
 void bap_destroy(bap_option *opt);

@@ -22,10 +22,14 @@ PAYOFF_CODE = {"max_call": 0, "basket_put": 1, "geo_call": 2}
 PURPOSE_IZ, PURPOSE_CMC, PURPOSE_TRAIN, PURPOSE_PRICE = 1, 2, 3, 4
 MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
-EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_fit_boundary", "bap_fit_classifier",
-            "bap_price", "bap_export_rules", "bap_import_rules", "bap_fit_points",
-            "bap_debug_continuation", "bap_debug_paths", "bap_debug_rng", "bap_destroy",
-            "bap_last_error", "bap_version"]
+EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
+            "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
+            "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
+            "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
+            "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait",
+            "bap_server_get_stats", "bap_server_destroy"]
+LAUNCH_PLAIN, LAUNCH_GRAPH = 0, 1
+METHOD_CODE = {"iz": 0, "cmc": 1}
 
 
 class BapError(RuntimeError):
@@ -58,7 +62,14 @@ class _Result(C.Structure):
                 ("fp64_delta", C.c_double), ("n_noconv", C.c_int), ("n_noroot", C.c_int),
                 ("fit_path_steps", C.c_int64), ("fit_ms", C.c_double), ("price_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("path_launches", C.c_int64),
-                ("path_kernel_ms", C.c_double)]
+                ("path_kernel_ms", C.c_double), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("queued", C.c_int64), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
+                ("peak_inflight", C.c_int64)]
 
 
 _lib = None
@@ -78,6 +89,16 @@ def lib():
         L.bap_create.argtypes = [C.POINTER(_Model), C.POINTER(vp)]
         L.bap_set_stream.argtypes = [vp, vp]
         L.bap_set_profiling.argtypes = [vp, C.c_int]
+        L.bap_set_launch_mode.argtypes = [vp, C.c_int]
+        L.bap_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
+        L.bap_server_set_launch_mode.argtypes = [vp, C.c_int]
+        L.bap_submit.argtypes = [vp, C.POINTER(_Model), C.c_int, vp, C.c_int64, C.c_uint64,
+                                 C.POINTER(C.c_uint64)]
+        L.bap_poll.argtypes = [vp, C.c_uint64, C.POINTER(_Result)]
+        L.bap_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(_Result)]
+        L.bap_server_get_stats.argtypes = [vp, C.POINTER(_ServerStats)]
+        L.bap_server_destroy.argtypes = [vp]
+        L.bap_server_destroy.restype = None
         L.bap_fit_boundary.argtypes = [vp, C.POINTER(_IZ)]
         L.bap_fit_classifier.argtypes = [vp, C.POINTER(_CMC)]
         L.bap_price.argtypes = [vp, C.c_int64, C.c_uint64, C.POINTER(_Result)]
@@ -95,7 +116,7 @@ def lib():
         L.bap_last_error.restype = C.c_char_p
         L.bap_version.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("bap_destroy", "bap_last_error", "bap_version"):
+            if name not in ("bap_destroy", "bap_last_error", "bap_version", "bap_server_destroy"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -119,20 +140,32 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _model(spec):
+    """The bap_model of an OptionSpec plus the arrays it points to (keep them alive)."""
+    keep = [_f64(spec.S0), _f64(spec.sigma), _f64(spec.delta), _f64(spec.rho)]
+    dates = None if spec.dates is None else _f64(spec.dates)
+    w = None if spec.weights is None else _f64(spec.weights)
+    keep += [dates, w]
+    m = _Model(spec.d, _dp(keep[0]), _dp(keep[1]), _dp(keep[2]), _dp(keep[3]), spec.r, spec.K,
+               spec.T, spec.n_dates, None if dates is None else _dp(dates),
+               PAYOFF_CODE[spec.payoff], None if w is None else _dp(w))
+    return m, keep
+
+
+def _params(p):
+    if hasattr(p, "N1"):
+        return 0, _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point,
+                      p.fp_eps)
+    return 1, _CMC(p.J, p.N2, p.n_stumps, p.seed)
+
+
 class Option:
     """An option on the device: bap_create / bap_fit_boundary / bap_fit_classifier / bap_price."""
 
     def __init__(self, spec, stream: Optional[int] = None):
         L = lib()
         self.spec = spec
-        self._keep = [_f64(spec.S0), _f64(spec.sigma), _f64(spec.delta), _f64(spec.rho)]
-        dates = None if spec.dates is None else _f64(spec.dates)
-        w = None if spec.weights is None else _f64(spec.weights)
-        self._keep += [dates, w]
-        m = _Model(spec.d, _dp(self._keep[0]), _dp(self._keep[1]), _dp(self._keep[2]),
-                   _dp(self._keep[3]), spec.r, spec.K, spec.T, spec.n_dates,
-                   None if dates is None else _dp(dates), PAYOFF_CODE[spec.payoff],
-                   None if w is None else _dp(w))
+        m, self._keep = _model(spec)
         h = C.c_void_p()
         _check(L.bap_create(C.byref(m), C.byref(h)))
         self.h = h
@@ -155,6 +188,9 @@ class Option:
 
     def set_profiling(self, on: bool):
         _check(lib().bap_set_profiling(self.h, 1 if on else 0))
+
+    def set_launch_mode(self, mode: int):
+        _check(lib().bap_set_launch_mode(self.h, mode))
 
     def fit_boundary(self, p) -> int:
         c = _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point, p.fp_eps)
@@ -209,6 +245,57 @@ class Option:
         _check(lib().bap_debug_paths(self.h, m, purpose, seed, item_id, _dp(start), N, _ip(tau),
                                      _dp(phi)))
         return tau, phi
+
+
+class Server:
+    """Continuous-batching server: bap_server_create / bap_submit / bap_poll / bap_wait."""
+
+    def __init__(self, device_mem_budget: int = 8 << 30, max_inflight: int = 32):
+        h = C.c_void_p()
+        _check(lib().bap_server_create(device_mem_budget, max_inflight, C.byref(h)))
+        self.h = h
+
+    def set_launch_mode(self, mode: int):
+        _check(lib().bap_server_set_launch_mode(self.h, mode))
+
+    def submit(self, spec, params, n_paths: int, seed: int) -> int:
+        m, keep = _model(spec)
+        method, cp = _params(params)
+        t = C.c_uint64(0)
+        _check(lib().bap_submit(self.h, C.byref(m), method, C.cast(C.byref(cp), C.c_void_p),
+                                n_paths, seed, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while not ready; else (status, result dict)."""
+        r = _Result()
+        st = lib().bap_poll(self.h, ticket, C.byref(r))
+        if st == BAP_ENOTREADY:
+            return None
+        _check(st, (BAP_OK, BAP_ENOCONV))
+        return st, {k: getattr(r, k) for k, _ in _Result._fields_}
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        r = _Result()
+        st = lib().bap_wait(self.h, ticket, timeout_s, C.byref(r))
+        _check(st, (BAP_OK, BAP_ENOCONV))
+        return st, {k: getattr(r, k) for k, _ in _Result._fields_}
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib().bap_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().bap_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def debug_rng(seed: int, purpose: int, m: int, w1: int, step: int, d: int, count: int):

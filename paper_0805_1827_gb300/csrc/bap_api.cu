@@ -3,25 +3,20 @@
 // The host validates arguments, owns device buffers and enqueues kernels on the option's
 // stream.  Every step of the method (Cholesky, lattice, Newton iterations, regression,
 // training points, boosting, pricing) runs in device kernels; the host reads back only the
-// results a call returns.
+// results a call returns.  Fits and pricing are split into an enqueue part (asynchronous on the
+// option's stream, results into page-locked host memory) and a finish part, so that the serving
+// loop can keep many options in flight.
 #include <algorithm>
 #include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <mutex>
-#include <string>
 #include <unordered_map>
-#include <vector>
 
-#include "bap_fit.cuh"
-#include "bap_path.cuh"
+#include "bap_host.cuh"
 
 using namespace bap;
 
-namespace {
+namespace bap {
 
-thread_local std::string g_err;
+static thread_local std::string g_err;
 
 bap_status fail(bap_status st, const char* fmt, ...) {
     char buf[512];
@@ -33,38 +28,55 @@ bap_status fail(bap_status st, const char* fmt, ...) {
     return st;
 }
 
-#define CU(call)                                                                             \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
-            return fail(e_ == cudaErrorMemoryAllocation ? BAP_ENOMEM : BAP_ECUDA,            \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
+void clear_error() { g_err.clear(); }
 
-#define TRY(expr)                          \
-    do {                                   \
-        bap_status s_ = (expr);            \
-        if (s_ != BAP_OK) return s_;       \
-    } while (0)
+cudaStream_t& alloc_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
 
-// A device buffer that grows on demand.
-struct DevBuf {
-    void* p = nullptr;
-    size_t n = 0;
-    ~DevBuf() { if (p) cudaFree(p); }
-    bap_status reserve(size_t bytes) {
-        if (bytes <= n) return BAP_OK;
-        if (p) { cudaFree(p); p = nullptr; n = 0; }
-        cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            return fail(BAP_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
-        }
-        n = bytes < 256 ? 256 : bytes;
-        return BAP_OK;
+static std::mutex g_pin_mu;
+static std::vector<PinnedOut*> g_pin_free;
+
+PinnedOut* pinned_get() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        const int n = 256;
+        PinnedOut* slab = nullptr;
+        if (cudaMallocHost(&slab, sizeof(PinnedOut) * n) != cudaSuccess) return nullptr;
+        for (int i = n - 1; i >= 0; --i) g_pin_free.push_back(slab + i);
     }
-    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
-};
+    PinnedOut* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pinned_put(PinnedOut* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
+// Keep freed pool memory cached in the process (a process-local pool attribute), so that the
+// stream-ordered allocations of successive options reuse it instead of returning it.
+void keep_pool_cached(int dev) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+const char* error_text() { return g_err.c_str(); }
+
+}  // namespace bap
+
+namespace {
 
 constexpr int kBlock = 256;
 
@@ -90,49 +102,6 @@ const void* path_fn(int D, int rule, bool fp64) {
         default: return nullptr;
     }
 }
-
-}  // namespace
-
-// ---------------------------------------------------------------------------------------------
-
-struct bap_option {
-    int device = 0;
-    int sm_count = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;
-    // model (host copies)
-    int d = 0, n_dates = 0, payoff = 0;
-    double r = 0, K = 0, T = 0;
-    DevModel hm{};                // host copy after device set-up
-    DevBuf dmodel;
-    // rule
-    int rule_kind = R_NONE;
-    int n_bnd = 1, degree = 0, n_coef = 1;
-    int max_stumps = 0, rec_len = 0;
-    DevBuf fitted;                // int[n_dates+1]
-    DevBuf coef64, coef_f, coef_d;
-    DevBuf n_stumps, feat, thr, pol, alpha, rec_f, rec_d;
-    // fit state and scratch
-    int method = -1;              // last fit: 0 I&Z, 1 CMC
-    int n_items = 0;
-    DevBuf start, state, pivot, ctr_item, active0, active1, counts, work, partial,
-        partial_steps, done, total_steps, korobov_a, merit, label_y, label, sorted_v, sorted_i,
-        err, out_sums, out_steps, trace_tau, trace_phi, diag_x, diag_it, diag_st, stat_counts,
-        one;
-    int last_noconv = 0, last_noroot = 0;
-    long long last_fit_steps = 0;
-    double last_fit_ms = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // launch accounting and optional per-launch timing of the path kernel
-    long long launches = 0, path_launches = 0;
-    long long fit_launches = 0, fit_path_launches = 0;
-    double fit_path_ms = 0;
-    int profiling = 0;
-    std::vector<cudaEvent_t> prof_ev;
-    size_t prof_used = 0;
-};
-
-namespace {
 
 bool has_device(int* dev) {
     int n = 0;
@@ -180,7 +149,7 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
     void* args[] = {&a};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool timed = o->profiling && !fp64;
+    const bool timed = o->profiling && !fp64 && !o->capturing;
     if (timed) {
         while (o->prof_ev.size() < o->prof_used + 2) {
             cudaEvent_t e;
@@ -240,7 +209,6 @@ void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
         a.rule_stride = o->n_bnd * iz_stage_stride(o->d);
         a.n_bnd = o->n_bnd;
         a.n_coef = iz_stage_stride(o->d);
-        a.degree = o->degree;
     } else if (o->rule_kind == R_CMC) {
         a.rule_src = fp64 ? (const void*)o->rec_d.p : (const void*)o->rec_f.p;
         a.rule_stride = o->rec_len;
@@ -290,7 +258,7 @@ bap_status set_rule_cmc(bap_option* o, int max_stumps) {
 }
 
 // Scratch for n items of N paths each.
-bap_status reserve_items(bap_option* o, int n, long long N, int C, int max_iter) {
+bap_status reserve_items(bap_option* o, int n, int C, int max_iter) {
     const int d = o->d;
     TRY(o->start.reserve((size_t)n * d * 8));
     TRY(o->state.reserve((size_t)n * sizeof(ItemState)));
@@ -307,7 +275,7 @@ bap_status reserve_items(bap_option* o, int n, long long N, int C, int max_iter)
     TRY(o->out_steps.reserve((size_t)n * 8));
     TRY(o->label_y.reserve((size_t)n * 8));
     TRY(o->label.reserve((size_t)n * 4));
-    (void)N;
+    TRY(o->iterstate.reserve(sizeof(IterState)));
     return BAP_OK;
 }
 
@@ -324,29 +292,256 @@ bap_status record_diag(bap_option* o, int m, bool iz) {
             o->state.as<ItemState>(), n, o->diag_x.as<double>() + (size_t)m * n,
             o->diag_it.as<int>() + (size_t)m * n, o->diag_st.as<int>() + (size_t)m * n,
             o->stat_counts.as<int>());
-        ++o->launches;
     } else {
         collect_labels_kernel<<<g, 256, 0, o->stream>>>(
             o->label_y.as<double>(), n, o->diag_x.as<double>() + (size_t)m * n,
             o->diag_it.as<int>() + (size_t)m * n, o->diag_st.as<int>() + (size_t)m * n);
+    }
+    ++o->launches;
+    CU(cudaGetLastError());
+    return BAP_OK;
+}
+
+// One Newton pass of date m.  Plain form: iterate `it` uses the explicit ping-pong lists and
+// its own count and unit counter.  Device-decided form (it < 0): the kernel selects them from
+// the iteration state, which newton_decide_kernel advances.
+bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int it, int chunk,
+                               int C) {
+    PathArgs a;
+    base_args(o, a, m, MODE_NEWTON, false);
+    a.rk = make_round_keys(p->seed, P_IZ, (uint32_t)m);
+    a.N = p->N1;
+    a.chunk = chunk;
+    a.C = C;
+    if (it >= 0) {
+        a.active = (it & 1) ? o->active1.as<int>() : o->active0.as<int>();
+        a.n_active = o->counts.as<int>() + it;
+        a.work = o->work.as<unsigned long long>() + it;
+        a.next_active = (it & 1) ? o->active0.as<int>() : o->active1.as<int>();
+        a.next_count = o->counts.as<int>() + it + 1;
+    } else {
+        IterState* is = o->iterstate.as<IterState>();
+        a.iter_ptr = &is->iter;
+        a.list_pp[0] = o->active0.as<int>();
+        a.list_pp[1] = o->active1.as<int>();
+        a.count_pp = is->count;
+        a.work = &is->work;
+        a.n_active = is->count;     // unused when iter_ptr is set
+    }
+    a.start = o->start.as<double>();
+    a.ctr_item = o->ctr_item.as<int>();
+    a.pivot = o->pivot.as<int>();
+    a.partial = o->partial.as<double>();
+    a.partial_steps = o->partial_steps.as<long long>();
+    a.done = o->done.as<int>();
+    a.state = o->state.as<ItemState>();
+    a.f_tol = p->f_tol;
+    a.x_tol = p->x_tol;
+    a.fp_eps = p->fp_eps;
+    a.max_iter = p->max_iter;
+    a.fixed_point = p->fixed_point;
+    return launch_path(o, a, R_IZ, false, (long long)o->n_items * C);
+}
+
+bap_status enqueue_iz_prologue(bap_option* o, const bap_iz_params* p) {
+    const int n = o->n_items, J = p->J, s = o->d - 1;
+    cudaStream_t st = o->stream;
+    CU(cudaMemsetAsync(o->diag_x.p, 0, (size_t)(o->n_dates + 1) * n * 8, st));
+    CU(cudaMemsetAsync(o->diag_it.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->diag_st.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
+    iota_kernel<<<(n + 255) / 256, 256, 0, st>>>(o->ctr_item.as<int>(), n);
+    ++o->launches;
+    if (s >= 2 && J > 2) {
+        const int warps = J - 1;
+        korobov_merit_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(J, s, o->merit.as<double>());
         ++o->launches;
     }
+    korobov_pick_kernel<<<1, 256, 0, st>>>(J, s, o->merit.as<double>(), o->korobov_a.as<int>());
+    ++o->launches;
     CU(cudaGetLastError());
+    return BAP_OK;
+}
+
+bap_status enqueue_iz_setup(bap_option* o, const bap_iz_params* p, int m, bool device_loop) {
+    cudaStream_t st = o->stream;
+    int* count0;
+    if (device_loop) {
+        CU(cudaMemsetAsync(o->iterstate.p, 0, sizeof(IterState), st));
+        count0 = o->iterstate.as<IterState>()->count;
+    } else {
+        CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
+        CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
+        count0 = o->counts.as<int>();
+    }
+    iz_setup_kernel<<<(o->n_items + 127) / 128, 128, 0, st>>>(
+        o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
+        o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), count0);
+    ++o->launches;
+    CU(cudaGetLastError());
+    return BAP_OK;
+}
+
+bap_status enqueue_iz_fit_date_end(bap_option* o, const bap_iz_params* p, int m) {
+    ls_fit_kernel<<<o->n_bnd, 256, 0, o->stream>>>(
+        o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->degree, o->n_coef, o->start.as<double>(),
+        o->state.as<ItemState>(), o->coef64.as<double>(), o->coef_f.as<float>(),
+        o->coef_d.as<double>(), o->fitted.as<int>());
+    ++o->launches;
+    CU(cudaGetLastError());
+    return record_diag(o, m, true);
+}
+
+// The whole I&Z fit as one graph: per date the item set-up, a conditional while node whose body
+// is one Newton pass followed by newton_decide_kernel, then the regression and diagnostics.
+bap_status build_iz_graph(bap_option* o, const bap_iz_params* p, int chunk, int C) {
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    cudaStream_t st = o->stream;
+    o->capturing = 1;
+    bap_status status = BAP_OK;
+    auto abort_capture = [&]() {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(st, &junk);
+        if (junk && junk != g) cudaGraphDestroy(junk);
+    };
+    cudaError_t e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        o->capturing = 0;
+        cudaGraphDestroy(g);
+        return fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e));
+    }
+    status = enqueue_iz_prologue(o, p);
+    for (int m = o->n_dates - 1; m >= 1 && status == BAP_OK; --m) {
+        status = enqueue_iz_setup(o, p, m, true);
+        if (status != BAP_OK) break;
+        // frontier of the capture so far
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+        std::vector<cudaGraphNode_t> frontier(deps, deps + ndeps);
+        cudaGraph_t gg = nullptr;
+        if (e == cudaSuccess) e = cudaStreamEndCapture(st, &gg);
+        if (e != cudaSuccess) { status = fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e)); break; }
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, g, frontier.data(), nullptr, frontier.size(), &np);
+        if (e != cudaSuccess) { status = fail(BAP_ECUDA, "conditional node: %s", cudaGetErrorString(e)); break; }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { status = fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e)); break; }
+        status = enqueue_newton_pass(o, p, m, -1, chunk, C);
+        if (status == BAP_OK) {
+            newton_decide_kernel<<<1, 32, 0, st>>>(o->iterstate.as<IterState>(), p->max_iter, h,
+                                                   o->stat_counts.as<int>() + 2);
+            ++o->launches;
+            if (cudaGetLastError() != cudaSuccess) status = fail(BAP_ECUDA, "decide kernel");
+        }
+        cudaGraph_t bb = nullptr;
+        e = cudaStreamEndCapture(st, &bb);
+        if (status != BAP_OK) break;
+        if (e != cudaSuccess) { status = fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e)); break; }
+        e = cudaStreamBeginCaptureToGraph(st, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { status = fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e)); break; }
+        status = enqueue_iz_fit_date_end(o, p, m);
+    }
+    if (status != BAP_OK) {
+        abort_capture();
+        o->capturing = 0;
+        cudaGraphDestroy(g);
+        return status;
+    }
+    cudaGraph_t gend = nullptr;
+    e = cudaStreamEndCapture(st, &gend);
+    o->capturing = 0;
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(BAP_ECUDA, "capture end: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(BAP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    o->graph_exec = ex;
+    o->graph_params = *p;
+    return BAP_OK;
+}
+
+bool same_iz(const bap_iz_params& a, const bap_iz_params& b) {
+    return a.J == b.J && a.N1 == b.N1 && a.f_tol == b.f_tol && a.x_tol == b.x_tol &&
+           a.max_iter == b.max_iter && a.degree == b.degree && a.seed == b.seed &&
+           a.fixed_point == b.fixed_point && a.fp_eps == b.fp_eps;
+}
+
+bap_status run_sums_enqueue(bap_option* o, int m, int mode, bool fp64, const RoundKeys& rk,
+                            int n_items, long long N, const int* d_item_ids, const int* d_pivots,
+                            double* d_start, double* d_out_sums, long long* d_out_steps) {
+    const int chunk = choose_chunk(n_items, N);
+    const int C = (int)((N + chunk - 1) / chunk);
+    TRY(o->partial.reserve((size_t)n_items * C * 3 * 8));
+    TRY(o->partial_steps.reserve((size_t)n_items * C * 8));
+    TRY(o->done.reserve((size_t)n_items * 4));
+    TRY(o->work.reserve(16));
+    TRY(o->counts.reserve(16));
+    cudaStream_t st = o->stream;
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n_items * 4, st));
+    CU(cudaMemsetAsync(o->work.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    set_int_kernel<<<1, 32, 0, st>>>(o->counts.as<int>(), n_items);
+    ++o->launches;
+    PathArgs a;
+    base_args(o, a, m, mode, fp64);
+    a.rk = rk;
+    a.N = N;
+    a.chunk = chunk;
+    a.C = C;
+    a.active = nullptr;
+    a.n_active = o->counts.as<int>();
+    a.work = o->work.as<unsigned long long>();
+    a.start = d_start;
+    a.ctr_item = d_item_ids;
+    a.pivot = d_pivots;
+    a.partial = o->partial.as<double>();
+    a.partial_steps = o->partial_steps.as<long long>();
+    a.done = o->done.as<int>();
+    a.out_sums = d_out_sums;
+    a.out_steps = d_out_steps;
+    a.trace_tau = o->trace_tau.as<int>();
+    a.trace_phi = o->trace_phi.as<double>();
+    return launch_path(o, a, o->rule_kind, fp64, (long long)n_items * C);
+}
+
+bap_status run_sums(bap_option* o, int m, int mode, bool fp64, const RoundKeys& rk, int n_items,
+                    long long N, const int* d_item_ids, const int* d_pivots, double* d_start,
+                    double* h_sums, long long* h_steps) {
+    TRY(o->out_sums.reserve((size_t)n_items * 3 * 8));
+    TRY(o->out_steps.reserve((size_t)n_items * 8));
+    TRY(run_sums_enqueue(o, m, mode, fp64, rk, n_items, N, d_item_ids, d_pivots, d_start,
+                         o->out_sums.as<double>(), o->out_steps.as<long long>()));
+    cudaStream_t st = o->stream;
+    CU(cudaMemcpyAsync(h_sums, o->out_sums.p, (size_t)n_items * 3 * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(h_steps, o->out_steps.p, (size_t)n_items * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
     return BAP_OK;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// Building blocks shared with the serving loop.
 
-extern "C" {
+namespace bap {
 
-const char* bap_last_error(void) { return g_err.c_str(); }
-
-const char* bap_version(void) { return "bap-gb300 1.0 (sm_103a)"; }
-
-bap_status bap_create(const bap_model* md, bap_option** out) {
-    g_err.clear();
+bap_status option_create(const bap_model* md, bap_option** out) {
     if (!md || !out) return fail(BAP_EINVAL, "null argument");
     *out = nullptr;
     const int d = md->d;
@@ -400,30 +595,42 @@ bap_status bap_create(const bap_model* md, bap_option** out) {
     o->r = md->r;
     o->K = md->K;
     o->T = md->T;
-    auto cleanup = [&](bap_status s) { bap_destroy(o); return s; };
+    // temporaries of the set-up; released before the option (and its stream) on every path
+    DevBuf drho, dstatus;
+    auto cleanup = [&](bap_status s) {
+        drho.release(o->stream);
+        dstatus.release(o->stream);
+        option_destroy(o);
+        return s;
+    };
+    keep_pool_cached(dev);
     cudaError_t e = cudaDeviceGetAttribute(&o->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
     e = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
     o->stream = o->own_stream;
-    if (cudaEventCreate(&o->ev0) != cudaSuccess || cudaEventCreate(&o->ev1) != cudaSuccess)
+    AllocScope scope(o->stream);
+    if (cudaEventCreate(&o->ev0) != cudaSuccess || cudaEventCreate(&o->ev1) != cudaSuccess ||
+        cudaEventCreate(&o->ev2) != cudaSuccess || cudaEventCreate(&o->ev3) != cudaSuccess)
         return cleanup(fail(BAP_ECUDA, "event create"));
+    o->pin = pinned_get();
+    if (!o->pin) return cleanup(fail(BAP_ENOMEM, "page-locked host allocation"));
+    memset(o->pin, 0, sizeof(PinnedOut));
     bap_status st;
     if ((st = o->dmodel.reserve(sizeof(DevModel))) != BAP_OK) return cleanup(st);
+    if ((st = o->s0buf.reserve((size_t)d * 8)) != BAP_OK) return cleanup(st);
     if ((st = o->fitted.reserve((md->n_dates + 1) * sizeof(int))) != BAP_OK) return cleanup(st);
     if ((st = o->total_steps.reserve(8)) != BAP_OK) return cleanup(st);
     if ((st = o->stat_counts.reserve(16)) != BAP_OK) return cleanup(st);
     if ((st = o->one.reserve(8)) != BAP_OK) return cleanup(st);
-    DevBuf drho;
     if ((st = drho.reserve((size_t)d * d * 8)) != BAP_OK) return cleanup(st);
-    DevBuf dstatus;
     if ((st = dstatus.reserve(4)) != BAP_OK) return cleanup(st);
     e = cudaMemcpyAsync(o->dmodel.p, &hm, sizeof hm, cudaMemcpyHostToDevice, o->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(drho.p, md->rho, (size_t)d * d * 8, cudaMemcpyHostToDevice, o->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(o->fitted.p, 0, (md->n_dates + 1) * sizeof(int), o->stream);
     if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
     model_setup_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), drho.as<double>(), dstatus.as<int>());
-    ++o->launches;
+    copy_s0_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), o->s0buf.as<double>());
     int status = -1;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&o->hm, o->dmodel.p, sizeof(DevModel), cudaMemcpyDeviceToHost, o->stream);
@@ -431,160 +638,147 @@ bap_status bap_create(const bap_model* md, bap_option** out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(o->stream);
     if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
     if (status != 0) return cleanup(fail(BAP_EINVAL, "rho is not positive definite"));
+    drho.release(o->stream);
+    dstatus.release(o->stream);
     *out = o;
     return BAP_OK;
 }
 
-bap_status bap_set_stream(bap_option* o, void* s) {
-    if (!o) return fail(BAP_EINVAL, "null option");
-    o->stream = reinterpret_cast<cudaStream_t>(s);
-    return BAP_OK;
-}
-
-bap_status bap_set_profiling(bap_option* o, int on) {
-    if (!o) return fail(BAP_EINVAL, "null option");
-    o->profiling = on ? 1 : 0;
-    o->prof_used = 0;
-    return BAP_OK;
-}
-
-void bap_destroy(bap_option* o) {
+void option_destroy(bap_option* o) {
     if (!o) return;
     if (o->stream) cudaStreamSynchronize(o->stream);
+    // the option is idle: return its memory to the pool in the order of its own stream
+    cudaStream_t own = o->own_stream;
+    o->for_each_buf([&](DevBuf& b) { b.release(own); });
     for (cudaEvent_t e : o->prof_ev) cudaEventDestroy(e);
+    if (o->graph_exec) cudaGraphExecDestroy(o->graph_exec);
     if (o->ev0) cudaEventDestroy(o->ev0);
     if (o->ev1) cudaEventDestroy(o->ev1);
-    if (o->own_stream) cudaStreamDestroy(o->own_stream);
+    if (o->ev2) cudaEventDestroy(o->ev2);
+    if (o->ev3) cudaEventDestroy(o->ev3);
+    pinned_put(o->pin);
     delete o;
+    if (own) cudaStreamDestroy(own);
 }
 
-bap_status bap_fit_boundary(bap_option* o, const bap_iz_params* p) {
-    g_err.clear();
-    if (!o || !p) return fail(BAP_EINVAL, "null argument");
+bap_status validate_iz(const bap_option* o, const bap_iz_params* p) {
+    (void)o;
+    if (!p) return fail(BAP_EINVAL, "null argument");
     if (p->J < 1 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 1..8192", p->J);
     if (p->N1 < 1 || p->N1 > (1LL << 31)) return fail(BAP_EINVAL, "N1 outside 1..2^31");
     if (p->max_iter < 1 || p->max_iter > 200) return fail(BAP_EINVAL, "max_iter outside 1..200");
     if (p->degree < 0 || p->degree > 2) return fail(BAP_EINVAL, "degree outside 0..2");
     if (!(p->f_tol >= 0) || !(p->x_tol >= 0)) return fail(BAP_EINVAL, "negative tolerance");
     if (p->fixed_point && !(p->fp_eps > 0)) return fail(BAP_EINVAL, "fp_eps must be positive");
-    if (o->n_dates < 2) {
-        TRY(set_rule_iz(o, p->degree));
-        o->method = 0;
-        o->n_items = 0;
-        o->last_fit_steps = 0;
-        o->last_noconv = o->last_noroot = 0;
-        return BAP_OK;
-    }
-    const int d = o->d, s = d - 1;
+    return BAP_OK;
+}
+
+bap_status validate_cmc(const bap_option* o, const bap_cmc_params* p) {
+    (void)o;
+    if (!p) return fail(BAP_EINVAL, "null argument");
+    if (p->J < 2 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 2..8192", p->J);
+    if (p->N2 < 1 || p->N2 > (1LL << 31)) return fail(BAP_EINVAL, "N2 outside 1..2^31");
+    if (p->n_stumps < 1 || p->n_stumps > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "n_stumps outside 1..%d", BAP_MAX_STUMPS);
+    return BAP_OK;
+}
+
+bap_status validate_price(const bap_option* o, int64_t n_paths) {
+    if (!o) return fail(BAP_EINVAL, "null argument");
+    if (n_paths < 2 || n_paths > (1LL << 40)) return fail(BAP_EINVAL, "n_paths outside 2..2^40");
+    return BAP_OK;
+}
+
+bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
+    AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
     o->prof_used = 0;
     TRY(set_rule_iz(o, p->degree));
+    o->method = 0;
+    if (o->n_dates < 2) {
+        o->n_items = 0;
+        memset(o->pin, 0, sizeof(PinnedOut));
+        CU(cudaEventRecord(o->ev0, o->stream));
+        CU(cudaEventRecord(o->ev1, o->stream));
+        return BAP_OK;
+    }
     const int J = p->J;
     const int n = o->n_bnd * J;
     o->n_items = n;
     const int chunk = choose_chunk(n, p->N1);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
-    TRY(reserve_items(o, n, p->N1, C, p->max_iter));
+    TRY(reserve_items(o, n, C, p->max_iter));
     TRY(o->korobov_a.reserve(8));
     TRY(o->merit.reserve((size_t)(J + 1) * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
     TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
     TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
     cudaStream_t st = o->stream;
-    CU(cudaMemsetAsync(o->diag_x.p, 0, (size_t)(o->n_dates + 1) * n * 8, st));
-    CU(cudaMemsetAsync(o->diag_it.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
-    CU(cudaMemsetAsync(o->diag_st.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
-    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
-    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
-    CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
-    iota_kernel<<<(n + 255) / 256, 256, 0, st>>>(o->ctr_item.as<int>(), n);
-    ++o->launches;
-    CU(cudaEventRecord(o->ev0, st));
-    // [glp]
-    if (s >= 2 && J > 2) {
-        const int warps = J - 1;
-        korobov_merit_kernel<<<(warps * 32 + 255) / 256, 256, 0, st>>>(J, s, o->merit.as<double>());
-        ++o->launches;
-    }
-    korobov_pick_kernel<<<1, 256, 0, st>>>(J, s, o->merit.as<double>(), o->korobov_a.as<int>());
-    ++o->launches;
-    CU(cudaGetLastError());
-    const RoundKeys rk0 = make_round_keys(p->seed, P_IZ, 0);
-    (void)rk0;
-    for (int m = o->n_dates - 1; m >= 1; --m) {
-        CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
-        CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
-        iz_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(
-            o->dmodel.as<DevModel>(), m, J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
-            o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), o->counts.as<int>());
-        ++o->launches;
-        CU(cudaGetLastError());
-        for (int it = 0; it < p->max_iter; ++it) {
-            PathArgs a;
-            base_args(o, a, m, MODE_NEWTON, false);
-            a.rk = make_round_keys(p->seed, P_IZ, (uint32_t)m);
-            a.N = p->N1;
-            a.chunk = chunk;
-            a.C = C;
-            a.active = (it & 1) ? o->active1.as<int>() : o->active0.as<int>();
-            a.n_active = o->counts.as<int>() + it;
-            a.work = o->work.as<unsigned long long>() + it;
-            a.start = o->start.as<double>();
-            a.ctr_item = o->ctr_item.as<int>();
-            a.pivot = o->pivot.as<int>();
-            a.partial = o->partial.as<double>();
-            a.partial_steps = o->partial_steps.as<long long>();
-            a.done = o->done.as<int>();
-            a.state = o->state.as<ItemState>();
-            a.next_active = (it & 1) ? o->active0.as<int>() : o->active1.as<int>();
-            a.next_count = o->counts.as<int>() + it + 1;
-            a.f_tol = p->f_tol;
-            a.x_tol = p->x_tol;
-            a.fp_eps = p->fp_eps;
-            a.max_iter = p->max_iter;
-            a.fixed_point = p->fixed_point;
-            TRY(launch_path(o, a, R_IZ, false, (long long)n * C));
+    bool use_graph = o->launch_mode == LAUNCH_GRAPH && !o->graph_failed && !o->profiling;
+    if (use_graph && (!o->graph_exec || !same_iz(o->graph_params, *p))) {
+        if (o->graph_exec) {
+            cudaGraphExecDestroy(o->graph_exec);
+            o->graph_exec = nullptr;
         }
-        ls_fit_kernel<<<o->n_bnd, 256, 0, st>>>(
-            o->dmodel.as<DevModel>(), m, J, o->n_bnd, o->degree, o->n_coef, o->start.as<double>(),
-            o->state.as<ItemState>(), o->coef64.as<double>(), o->coef_f.as<float>(),
-            o->coef_d.as<double>(), o->fitted.as<int>());
-        ++o->launches;
-        CU(cudaGetLastError());
-        TRY(record_diag(o, m, true));
+        const long long saved = o->launches, saved_p = o->path_launches;
+        if (build_iz_graph(o, p, chunk, C) != BAP_OK) {
+            o->graph_failed = 1;     // this device or driver cannot run it: use the plain form
+            use_graph = false;
+            cudaGetLastError();
+        }
+        o->launches = saved;
+        o->path_launches = saved_p;
+    }
+    CU(cudaEventRecord(o->ev0, st));
+    o->last_graph = use_graph ? 1 : 0;
+    if (use_graph) {
+        CU(cudaGraphLaunch(o->graph_exec, st));
+        // kernels in the graph: prologue (iota, lattice) + per date (set-up, LS, diagnostics);
+        // the Newton passes actually run (a path kernel and a decide kernel each) are counted on
+        // the device and added by finish_fit_iz
+        o->launches += 2 + (p->J > 2 && o->d >= 3) + 3LL * (o->n_dates - 1);
+    } else {
+        TRY(enqueue_iz_prologue(o, p));
+        for (int m = o->n_dates - 1; m >= 1; --m) {
+            TRY(enqueue_iz_setup(o, p, m, false));
+            for (int it = 0; it < p->max_iter; ++it) TRY(enqueue_newton_pass(o, p, m, it, chunk, C));
+            TRY(enqueue_iz_fit_date_end(o, p, m));
+        }
     }
     CU(cudaEventRecord(o->ev1, st));
-    unsigned long long steps = 0;
-    int counts[4] = {0, 0, 0, 0};
-    CU(cudaMemcpyAsync(&steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(counts, o->stat_counts.p, 16, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
+    CU(cudaMemcpyAsync(&o->pin->fit_steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(o->pin->counts, o->stat_counts.p, 16, cudaMemcpyDeviceToHost, st));
+    return BAP_OK;
+}
+
+bap_status finish_fit_iz(bap_option* o) {
     float ms = 0;
     CU(cudaEventElapsedTime(&ms, o->ev0, o->ev1));
     o->last_fit_ms = ms;
-    o->last_fit_steps = (long long)steps;
-    o->last_noconv = counts[0];
-    o->last_noroot = counts[1];
-    o->method = 0;
+    o->last_fit_steps = (long long)o->pin->fit_steps;
+    o->last_noconv = o->pin->counts[0];
+    o->last_noroot = o->pin->counts[1];
+    if (o->last_graph) {
+        o->launches += 2LL * o->pin->counts[2];
+        o->path_launches += o->pin->counts[2];
+    }
     o->fit_launches = o->launches;
     o->fit_path_launches = o->path_launches;
     o->fit_path_ms = prof_collect(o);
-    return counts[0] > 0 ? BAP_ENOCONV : BAP_OK;
+    return o->last_noconv > 0 ? BAP_ENOCONV : BAP_OK;
 }
 
-bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
-    g_err.clear();
-    if (!o || !p) return fail(BAP_EINVAL, "null argument");
-    if (p->J < 2 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 2..8192", p->J);
-    if (p->N2 < 1 || p->N2 > (1LL << 31)) return fail(BAP_EINVAL, "N2 outside 1..2^31");
-    if (p->n_stumps < 1 || p->n_stumps > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "n_stumps outside 1..%d", BAP_MAX_STUMPS);
+bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
+    AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
     o->prof_used = 0;
     TRY(set_rule_cmc(o, p->n_stumps));
     o->method = 1;
+    cudaStream_t st = o->stream;
     if (o->n_dates < 2) {
         o->n_items = 0;
-        o->last_fit_steps = 0;
+        memset(o->pin, 0, sizeof(PinnedOut));
+        CU(cudaEventRecord(o->ev0, st));
+        CU(cudaEventRecord(o->ev1, st));
         return BAP_OK;
     }
     const int J = p->J;
@@ -593,22 +787,22 @@ bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
     const int chunk = choose_chunk(n, p->N2);
     const int C = (int)((p->N2 + chunk - 1) / chunk);
     const int d = o->d, nF = d + 1;
-    TRY(reserve_items(o, n, p->N2, C, 1));
+    TRY(reserve_items(o, n, C, 1));
     TRY(o->sorted_v.reserve((size_t)nF * J * 8));
     TRY(o->sorted_i.reserve((size_t)nF * J * 4));
     TRY(o->err.reserve((size_t)nF * J * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
     TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
     TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
-    cudaStream_t st = o->stream;
     CU(cudaMemsetAsync(o->diag_x.p, 0, (size_t)(o->n_dates + 1) * n * 8, st));
     CU(cudaMemsetAsync(o->diag_it.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
     CU(cudaMemsetAsync(o->diag_st.p, 0, (size_t)(o->n_dates + 1) * n * 4, st));
     CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
     CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
     int P2 = 1;
     while (P2 < J) P2 <<= 1;
-    const size_t ab_smem = (size_t)J * 8 + (size_t)P2 * 12;
+    const size_t ab_smem = (size_t)J * 8 + std::max((size_t)P2 * 12, (size_t)J * 8) + (size_t)J + 16;
     CU(cudaFuncSetAttribute(adaboost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(ab_smem, 48 * 1024)));
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
@@ -649,13 +843,15 @@ bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
         TRY(record_diag(o, m, false));
     }
     CU(cudaEventRecord(o->ev1, st));
-    unsigned long long steps = 0;
-    CU(cudaMemcpyAsync(&steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
+    CU(cudaMemcpyAsync(&o->pin->fit_steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    return BAP_OK;
+}
+
+bap_status finish_fit_cmc(bap_option* o) {
     float ms = 0;
     CU(cudaEventElapsedTime(&ms, o->ev0, o->ev1));
     o->last_fit_ms = ms;
-    o->last_fit_steps = (long long)steps;
+    o->last_fit_steps = (long long)o->pin->fit_steps;
     o->last_noconv = o->last_noroot = 0;
     o->fit_launches = o->launches;
     o->fit_path_launches = o->path_launches;
@@ -663,82 +859,45 @@ bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
     return BAP_OK;
 }
 
-static bap_status run_sums(bap_option* o, int m, int mode, bool fp64, const RoundKeys& rk, int n_items,
-                           long long N, const int* d_item_ids, const int* d_pivots,
-                           double* d_start, double* h_sums, long long* h_steps, float* ms) {
-    const int chunk = choose_chunk(n_items, N);
-    const int C = (int)((N + chunk - 1) / chunk);
-    TRY(o->partial.reserve((size_t)n_items * C * 3 * 8));
-    TRY(o->partial_steps.reserve((size_t)n_items * C * 8));
-    TRY(o->done.reserve((size_t)n_items * 4));
-    TRY(o->out_sums.reserve((size_t)n_items * 3 * 8));
-    TRY(o->out_steps.reserve((size_t)n_items * 8));
-    TRY(o->work.reserve(16));
-    TRY(o->counts.reserve(16));
+bap_status enqueue_price(bap_option* o, int64_t n_paths, uint64_t seed) {
+    AllocScope scope(o->stream);
+    o->launches = o->path_launches = 0;
+    o->prof_used = 0;
+    o->price_n = n_paths;
+    TRY(o->out_sums.reserve(3 * 8));
+    TRY(o->out_steps.reserve(8));
+    TRY(o->out_sums64.reserve(3 * 8));
+    TRY(o->out_steps64.reserve(8));
+    const RoundKeys rk = make_round_keys(seed, P_PRICE, 0);
     cudaStream_t st = o->stream;
-    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n_items * 4, st));
-    CU(cudaMemsetAsync(o->work.p, 0, 8, st));
-    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
-    set_int_kernel<<<1, 32, 0, st>>>(o->counts.as<int>(), n_items);
-    ++o->launches;
-    PathArgs a;
-    base_args(o, a, m, mode, fp64);
-    a.rk = rk;
-    a.N = N;
-    a.chunk = chunk;
-    a.C = C;
-    a.active = nullptr;
-    a.n_active = o->counts.as<int>();
-    a.work = o->work.as<unsigned long long>();
-    a.start = d_start;
-    a.ctr_item = d_item_ids;
-    a.pivot = d_pivots;
-    a.partial = o->partial.as<double>();
-    a.partial_steps = o->partial_steps.as<long long>();
-    a.done = o->done.as<int>();
-    a.out_sums = o->out_sums.as<double>();
-    a.out_steps = o->out_steps.as<long long>();
-    a.trace_tau = o->trace_tau.as<int>();
-    a.trace_phi = o->trace_phi.as<double>();
-    if (ms) CU(cudaEventRecord(o->ev0, st));
-    TRY(launch_path(o, a, o->rule_kind, fp64, (long long)n_items * C));
-    if (ms) CU(cudaEventRecord(o->ev1, st));
-    CU(cudaMemcpyAsync(h_sums, o->out_sums.p, (size_t)n_items * 3 * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(h_steps, o->out_steps.p, (size_t)n_items * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (ms) CU(cudaEventElapsedTime(ms, o->ev0, o->ev1));
+    CU(cudaEventRecord(o->ev2, st));
+    TRY(run_sums_enqueue(o, 0, MODE_SUMS, false, rk, 1, n_paths, nullptr, nullptr,
+                         o->s0buf.as<double>(), o->out_sums.as<double>(), o->out_steps.as<long long>()));
+    CU(cudaEventRecord(o->ev3, st));
+    TRY(run_sums_enqueue(o, 0, MODE_SUMS, true, rk, 1, n_paths, nullptr, nullptr,
+                         o->s0buf.as<double>(), o->out_sums64.as<double>(), o->out_steps64.as<long long>()));
+    CU(cudaMemcpyAsync(o->pin->sums, o->out_sums.p, 3 * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&o->pin->steps, o->out_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(o->pin->sums64, o->out_sums64.p, 3 * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&o->pin->steps64, o->out_steps64.p, 8, cudaMemcpyDeviceToHost, st));
     return BAP_OK;
 }
 
-bap_status bap_price(bap_option* o, int64_t n_paths, uint64_t seed, bap_result* res) {
-    g_err.clear();
-    if (!o || !res) return fail(BAP_EINVAL, "null argument");
-    if (n_paths < 2 || n_paths > (1LL << 40)) return fail(BAP_EINVAL, "n_paths outside 2..2^40");
+bap_status finish_price(bap_option* o, bap_result* res) {
     memset(res, 0, sizeof *res);
-    o->launches = o->path_launches = 0;
-    o->prof_used = 0;
-    DevBuf s0;
-    TRY(s0.reserve((size_t)o->d * 8));
-    copy_s0_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), s0.as<double>());
-    ++o->launches;
-    CU(cudaGetLastError());
-    const RoundKeys rk = make_round_keys(seed, P_PRICE, 0);
-    double sums[3], sums64[3];
-    long long steps = 0, steps64 = 0;
     float ms = 0;
-    TRY(run_sums(o, 0, MODE_SUMS, false, rk, 1, n_paths, nullptr, nullptr, s0.as<double>(), sums, &steps, &ms));
-    TRY(run_sums(o, 0, MODE_SUMS, true, rk, 1, n_paths, nullptr, nullptr, s0.as<double>(), sums64, &steps64, nullptr));
-    const double N = (double)n_paths;
-    const double mean = sums[0] / N;
-    double var = (sums[1] - N * mean * mean) / (N - 1.0);
+    CU(cudaEventElapsedTime(&ms, o->ev2, o->ev3));
+    const double N = (double)o->price_n;
+    const double mean = o->pin->sums[0] / N;
+    double var = (o->pin->sums[1] - N * mean * mean) / (N - 1.0);
     if (var < 0) var = 0;
     res->price = mean;
     res->var = var;
     res->se = std::sqrt(var / N);
     res->ci95 = 1.96 * res->se;
-    res->n_paths = n_paths;
-    res->path_steps = steps;
-    res->fp64_delta = mean - sums64[0] / N;
+    res->n_paths = o->price_n;
+    res->path_steps = o->pin->steps;
+    res->fp64_delta = mean - o->pin->sums64[0] / N;
     res->n_noconv = o->last_noconv;
     res->n_noroot = o->last_noroot;
     res->fit_path_steps = o->last_fit_steps;
@@ -750,15 +909,103 @@ bap_status bap_price(bap_option* o, int64_t n_paths, uint64_t seed, bap_result* 
     return BAP_OK;
 }
 
+size_t estimate_bytes(const bap_model* md, int method, const void* params, int64_t n_paths) {
+    const size_t d = (size_t)md->d, nd = (size_t)md->n_dates + 1;
+    size_t n = 0, C = 0, extra = 0, rules = 0;
+    if (method == BAP_METHOD_IZ) {
+        const bap_iz_params* p = static_cast<const bap_iz_params*>(params);
+        const size_t nb = (md->payoff == BAP_MAX_CALL && md->d > 1) ? d : 1;
+        n = nb * (size_t)p->J;
+        C = (size_t)((p->N1 + choose_chunk((long long)n, p->N1) - 1) / choose_chunk((long long)n, p->N1));
+        extra = (size_t)(p->J + 1) * 8 + (size_t)(p->max_iter + 2) * 12;
+        rules = nd * nb * (size_t)(MAXCOEF + 4) * 20;
+    } else {
+        const bap_cmc_params* p = static_cast<const bap_cmc_params*>(params);
+        n = (size_t)p->J;
+        C = (size_t)((p->N2 + choose_chunk((long long)n, p->N2) - 1) / choose_chunk((long long)n, p->N2));
+        extra = (d + 1) * n * 20;
+        rules = nd * (size_t)p->n_stumps * 64;
+    }
+    const size_t items = n * (d * 8 + sizeof(ItemState) + 40) + n * C * 32 + nd * n * 16;
+    const size_t price_c = (size_t)((n_paths + choose_chunk(1, n_paths) - 1) / choose_chunk(1, n_paths));
+    return sizeof(DevModel) + items + extra + rules + std::max(price_c, C * n) * 32 + (1 << 16);
+}
+
+}  // namespace bap
+
+// ---------------------------------------------------------------------------------------------
+
+extern "C" {
+
+const char* bap_last_error(void) { return error_text(); }
+
+const char* bap_version(void) { return "bap-gb300 1.1 (sm_103a)"; }
+
+bap_status bap_create(const bap_model* md, bap_option** out) {
+    clear_error();
+    return option_create(md, out);
+}
+
+bap_status bap_set_stream(bap_option* o, void* s) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    CU(cudaStreamSynchronize(o->stream));   // nothing of the option is pending on the old stream
+    o->stream = reinterpret_cast<cudaStream_t>(s);
+    return BAP_OK;
+}
+
+bap_status bap_set_profiling(bap_option* o, int on) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    o->profiling = on ? 1 : 0;
+    o->prof_used = 0;
+    return BAP_OK;
+}
+
+bap_status bap_set_launch_mode(bap_option* o, int mode) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH) return fail(BAP_EINVAL, "bad launch mode");
+    o->launch_mode = mode;
+    return BAP_OK;
+}
+
+void bap_destroy(bap_option* o) { option_destroy(o); }
+
+bap_status bap_fit_boundary(bap_option* o, const bap_iz_params* p) {
+    clear_error();
+    if (!o) return fail(BAP_EINVAL, "null option");
+    TRY(validate_iz(o, p));
+    TRY(enqueue_fit_iz(o, p));
+    CU(cudaStreamSynchronize(o->stream));
+    return finish_fit_iz(o);
+}
+
+bap_status bap_fit_classifier(bap_option* o, const bap_cmc_params* p) {
+    clear_error();
+    if (!o) return fail(BAP_EINVAL, "null option");
+    TRY(validate_cmc(o, p));
+    TRY(enqueue_fit_cmc(o, p));
+    CU(cudaStreamSynchronize(o->stream));
+    return finish_fit_cmc(o);
+}
+
+bap_status bap_price(bap_option* o, int64_t n_paths, uint64_t seed, bap_result* res) {
+    clear_error();
+    if (!res) return fail(BAP_EINVAL, "null argument");
+    TRY(validate_price(o, n_paths));
+    TRY(enqueue_price(o, n_paths, seed));
+    CU(cudaStreamSynchronize(o->stream));
+    return finish_price(o, res);
+}
+
 bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t seed, int n_items,
                                   const int* item_ids, const int* pivots, const double* starts,
                                   int64_t N, double* sums, int64_t* steps) {
-    g_err.clear();
+    clear_error();
     if (!o || !item_ids || !starts || !sums || !steps) return fail(BAP_EINVAL, "null argument");
     if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
     if (n_items < 1 || N < 1 || N > (1LL << 31)) return fail(BAP_EINVAL, "bad n_items or N");
     if (purpose < 1 || purpose > 4) return fail(BAP_EINVAL, "bad purpose");
     const int d = o->d;
+    AllocScope scope(o->stream);
     for (int i = 0; i < n_items; ++i) {
         for (int q = 0; q < d; ++q)
             if (!(starts[(size_t)i * d + q] > 0)) return fail(BAP_EINVAL, "start points must be positive");
@@ -773,18 +1020,19 @@ bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t se
     if (pivots) CU(cudaMemcpyAsync(dp.p, pivots, (size_t)n_items * 4, cudaMemcpyHostToDevice, o->stream));
     std::vector<long long> st(n_items);
     TRY(run_sums(o, m, MODE_SUMS, false, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), n_items, N,
-                 di.as<int>(), pivots ? dp.as<int>() : nullptr, ds.as<double>(), sums, st.data(), nullptr));
+                 di.as<int>(), pivots ? dp.as<int>() : nullptr, ds.as<double>(), sums, st.data()));
     for (int i = 0; i < n_items; ++i) steps[i] = st[i];
     return BAP_OK;
 }
 
 bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int item_id,
                            const double* start, int64_t N, int* tau, double* disc_phi) {
-    g_err.clear();
+    clear_error();
     if (!o || !start || !tau || !disc_phi) return fail(BAP_EINVAL, "null argument");
     if (m < 0 || m >= o->n_dates) return fail(BAP_EINVAL, "bad m");
     if (N < 1 || N > (1LL << 26)) return fail(BAP_EINVAL, "N outside 1..2^26");
     const int d = o->d;
+    AllocScope scope(o->stream);
     DevBuf ds, di;
     TRY(ds.reserve((size_t)d * 8));
     TRY(di.reserve(4));
@@ -795,7 +1043,7 @@ bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int
     double sums[3];
     long long steps;
     TRY(run_sums(o, m, MODE_TRACE, false, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), 1, N,
-                 di.as<int>(), nullptr, ds.as<double>(), sums, &steps, nullptr));
+                 di.as<int>(), nullptr, ds.as<double>(), sums, &steps));
     CU(cudaMemcpy(tau, o->trace_tau.p, (size_t)N * 4, cudaMemcpyDeviceToHost));
     CU(cudaMemcpy(disc_phi, o->trace_phi.p, (size_t)N * 8, cudaMemcpyDeviceToHost));
     return BAP_OK;
@@ -803,11 +1051,12 @@ bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int
 
 bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_t step, int d,
                          int64_t count, uint32_t* words, double* z) {
-    g_err.clear();
+    clear_error();
     if (d < 1 || d > 16 || count < 1 || count > (1LL << 26)) return fail(BAP_EINVAL, "bad d or count");
     int dev;
     if (!has_device(&dev)) return fail(BAP_ECUDA, "no CUDA device");
     const int nc = (d + 3) / 4;
+    AllocScope scope(nullptr);
     DevBuf dw, dz;
     if (words) TRY(dw.reserve((size_t)count * nc * 16));
     if (z) TRY(dz.reserve((size_t)count * d * 8));
@@ -821,7 +1070,7 @@ bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_
 }
 
 bap_status bap_fit_points(const bap_option* o, int m, int* n_items, double* x, int* iters, int* status) {
-    g_err.clear();
+    clear_error();
     if (!o || !n_items) return fail(BAP_EINVAL, "null argument");
     if (o->method < 0) return fail(BAP_ESTATE, "no fit yet");
     if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "bad m");
@@ -839,7 +1088,7 @@ bap_status bap_fit_points(const bap_option* o, int m, int* n_items, double* x, i
 }
 
 bap_status bap_export_rules(const bap_option* o, double* buf, size_t* len) {
-    g_err.clear();
+    clear_error();
     if (!o || !len) return fail(BAP_EINVAL, "null argument");
     const int nd = o->n_dates + 1;
     const int kind = o->rule_kind;
@@ -884,8 +1133,9 @@ bap_status bap_export_rules(const bap_option* o, double* buf, size_t* len) {
 }
 
 bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
-    g_err.clear();
+    clear_error();
     if (!o || !buf || len < 6) return fail(BAP_EINVAL, "null or short buffer");
+    AllocScope scope(o->stream);
     const int kind = (int)buf[0];
     const int nd = o->n_dates + 1;
     if ((int)buf[1] != o->n_dates) return fail(BAP_EINVAL, "n_dates mismatch");
@@ -910,7 +1160,6 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
         stage_iz_kernel<<<(nd * o->n_bnd + 127) / 128, 128, 0, o->stream>>>(
             o->coef64.as<double>(), o->n_dates, o->n_bnd, o->n_coef, o->d - 1, o->degree, o->K,
             o->coef_f.as<float>(), o->coef_d.as<double>());
-        ++o->launches;
         CU(cudaGetLastError());
     } else if (kind == R_CMC) {
         const int ms = (int)buf[5];
@@ -940,7 +1189,6 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
         stage_cmc_kernel<<<(nd + 31) / 32, 32, 0, o->stream>>>(
             o->n_dates, o->d + 1, ms, o->n_stumps.as<int>(), o->feat.as<int>(), o->thr.as<double>(),
             o->pol.as<int>(), o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(), o->rec_d.as<double>());
-        ++o->launches;
         CU(cudaGetLastError());
     } else {
         return fail(BAP_EINVAL, "bad rule kind %d", kind);

@@ -465,9 +465,72 @@ __global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int*
 // distinct sorted values (polarity +1 then -1); with e_min the least weighted error the first
 // candidate with error <= e_min + 1e-12 wins.  alpha = 1/2 ln((1-eps)/eps) with eps clamped to
 // [1e-10, 1-1e-10]; stop before a stump with eps >= 1/2 and after a perfect one.
+//
+// The weights are FP64 and normalised every round; the weighted errors are summed exactly in
+// 64-bit fixed point (w 2^60, integer adds on the full-rate ALU instead of the narrow FP64
+// pipe), as one block-wide prefix scan per feature over contiguous segments of the sorted
+// order.  The update multiplies each weight by exp(-alpha) or exp(+alpha), the two values
+// exp(-alpha y h) takes.
 
 __device__ inline bool key_less(double a, int ia, double b, int ib) {
     return a < b || (a == b && ia < ib);
+}
+
+constexpr double kFix = 1152921504606846976.0;   // 2^60
+
+// Block-wide exclusive scan of two 64-bit values per thread (1024 threads); returns the block
+// totals through tot_a / tot_b.  Uses red_a / red_b (32 entries each) in shared memory.
+__device__ inline void block_scan2(long long& a, long long& b, long long* red_a, long long* red_b,
+                                   long long& tot_a, long long& tot_b) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long ia = a, ib = b;
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long ta = __shfl_up_sync(FULL, ia, off);
+        const long long tb = __shfl_up_sync(FULL, ib, off);
+        if (lane >= off) { ia += ta; ib += tb; }
+    }
+    if (lane == 31) { red_a[wid] = ia; red_b[wid] = ib; }
+    __syncthreads();
+    if (wid == 0) {
+        long long xa = lane < nw ? red_a[lane] : 0, xb = lane < nw ? red_b[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long ta = __shfl_up_sync(FULL, xa, off);
+            const long long tb = __shfl_up_sync(FULL, xb, off);
+            if (lane >= off) { xa += ta; xb += tb; }
+        }
+        red_a[lane] = xa;     // inclusive prefix of the warp totals
+        red_b[lane] = xb;
+    }
+    __syncthreads();
+    const long long base_a = wid > 0 ? red_a[wid - 1] : 0, base_b = wid > 0 ? red_b[wid - 1] : 0;
+    tot_a = red_a[nw - 1];
+    tot_b = red_b[nw - 1];
+    a = base_a + ia - a;      // exclusive
+    b = base_b + ib - b;
+    __syncthreads();
+}
+
+__device__ inline long long block_min_ll(long long v, long long* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_down_sync(0xffffffffu, v, off));
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    long long r = LLONG_MAX;
+    for (int k = 0; k < nw; ++k) r = min(r, red[k]);
+    __syncthreads();
+    return r;
+}
+
+__device__ inline double block_sum_d(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int k = 0; k < nw; ++k) r += red[k];
+    __syncthreads();
+    return r;
 }
 
 __global__ void __launch_bounds__(1024) adaboost_kernel(
@@ -476,24 +539,28 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
     int* feat, double* thr, int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d,
     int* fitted) {
     extern __shared__ __align__(16) unsigned char smem[];
+    (void)label_y;
     const int d = M->d;
     const int nF = d + 1;
     int P2 = 1;
     while (P2 < J) P2 <<= 1;
-    double* w = reinterpret_cast<double*>(smem);          // J
-    double* key = w + J;                                  // P2
-    int* idx = reinterpret_cast<int*>(key + P2);          // P2
-    __shared__ double wred[32];
-    __shared__ double fmin_e[MAXF];
-    __shared__ long long fcand[MAXF];
-    __shared__ double s_W, s_neg[MAXF], s_alpha, s_thr, s_e;
+    double* w = reinterpret_cast<double*>(smem);                         // J
+    unsigned char* region = smem + (size_t)J * 8;                        // sort keys, then wf
+    double* key = reinterpret_cast<double*>(region);                     // P2 (sorting only)
+    int* idx = reinterpret_cast<int*>(key + P2);                         // P2 (sorting only)
+    long long* wf = reinterpret_cast<long long*>(region);                // J (rounds only)
+    const size_t region_bytes = (size_t)P2 * 12 > (size_t)J * 8 ? (size_t)P2 * 12 : (size_t)J * 8;
+    signed char* lab = reinterpret_cast<signed char*>(region + region_bytes);   // J
+    long long* errl = reinterpret_cast<long long*>(err);                 // nF x J, -1 = no split
+    __shared__ long long red_a[32], red_b[32], red_m[32];
+    __shared__ double red_d[32];
+    __shared__ long long s_neg[MAXF];
+    __shared__ double s_alpha, s_thr, s_fok, s_fbad;
     __shared__ int s_f, s_pol, s_stop, s_count;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x;
 
-    // The payoff feature Phi(x_i) is recomputed in FP64 from the point (the same definition as
-    // the label epilogue of the path kernel).
-    // sort each feature (bitonic on (value, index))
+    // sort each feature (bitonic on (value, index)); the payoff feature is Phi in FP64 (the same
+    // definition as the label epilogue of the path kernel)
     for (int f = 0; f < nF; ++f) {
         for (int i = tid; i < P2; i += blockDim.x) {
             if (i < J) {
@@ -547,99 +614,83 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
         }
         __syncthreads();
     }
-    for (int i = tid; i < J; i += blockDim.x) w[i] = 1.0 / (double)J;
+    for (int i = tid; i < J; i += blockDim.x) {
+        w[i] = 1.0 / (double)J;
+        lab[i] = label[i] > 0 ? 1 : -1;
+    }
     if (tid == 0) s_count = 0;
     __syncthreads();
 
+    // contiguous segment of the sorted order per thread
+    const int per = (J + blockDim.x - 1) / blockDim.x;
+    const int lo = tid * per, hi = min(J, lo + per);
+    const long long tol = (long long)(1e-12 * kFix);
     const size_t o_st = (size_t)m * max_stumps;
     for (int round = 0; round < n_rounds; ++round) {
-        // W = sum of weights
-        double part = 0.0;
-        for (int i = tid; i < J; i += blockDim.x) part += w[i];
-        for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(FULL, part, off);
-        if (lane == 0) wred[wid] = part;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int k = 0; k < nw; ++k) t += wred[k];
-            s_W = t;
+        // fixed-point weights and their total
+        long long part = 0;
+        for (int i = tid; i < J; i += blockDim.x) {
+            const long long v = __double2ll_rn(w[i] * kFix);
+            wf[i] = v;
+            part += v;
         }
-        __syncthreads();
-        const double W = s_W;
-        // pass 1: one warp per feature scans its sorted order
-        for (int f = wid; f < nF; f += nw) {
-            const double* v = sorted_v + (size_t)f * J;
-            const int* ix = sorted_i + (size_t)f * J;
-            double neg = 0.0;
-            for (int i = lane; i < J; i += 32) neg += label[ix[i]] < 0 ? w[ix[i]] : 0.0;
-            for (int off = 16; off > 0; off >>= 1) neg += __shfl_down_sync(FULL, neg, off);
-            neg = __shfl_sync(FULL, neg, 0);
-            double cpos = 0.0, cneg = 0.0;      // running prefix carried across chunks
-            double emin = fmin(neg, W - neg);
-            for (int base = 0; base < J; base += 32) {
-                const int i = base + lane;
-                double ap = 0.0, an = 0.0;
-                if (i < J) {
-                    const double wi = w[ix[i]];
-                    if (label[ix[i]] > 0) ap = wi; else an = wi;
-                }
-                for (int off = 1; off < 32; off <<= 1) {
-                    const double tp = __shfl_up_sync(FULL, ap, off);
-                    const double tn = __shfl_up_sync(FULL, an, off);
-                    if (lane >= off) { ap += tp; an += tn; }
-                }
-                ap += cpos;
-                an += cneg;
-                double e = NAN;
-                if (i < J - 1 && v[i + 1] > v[i]) {
-                    e = ap + (neg - an);
-                    emin = fmin(emin, fmin(e, W - e));
-                }
-                if (i < J - 1) err[(size_t)f * J + i] = e;
-                cpos = __shfl_sync(FULL, ap, 31);
-                cneg = __shfl_sync(FULL, an, 31);
+        long long Wp = part, dummy = 0, Wtot = 0, dtot = 0;
+        block_scan2(Wp, dummy, red_a, red_b, Wtot, dtot);
+        const long long W = Wtot;
+        // pass 1: errors of every candidate, least error per feature
+        long long emin = LLONG_MAX;
+        for (int f = 0; f < nF; ++f) {
+            const int* six = sorted_i + (size_t)f * J;
+            const double* sv = sorted_v + (size_t)f * J;
+            long long sp = 0, sn = 0;
+            for (int i = lo; i < hi; ++i) {
+                const int k = six[i];
+                if (lab[k] > 0) sp += wf[k]; else sn += wf[k];
             }
-            for (int off = 16; off > 0; off >>= 1) emin = fmin(emin, __shfl_down_sync(FULL, emin, off));
-            if (lane == 0) { fmin_e[f] = emin; s_neg[f] = neg; }
+            long long pp = sp, pn = sn, tot_p = 0, tot_n = 0;
+            block_scan2(pp, pn, red_a, red_b, tot_p, tot_n);
+            const long long neg = tot_n;
+            if (tid == 0) s_neg[f] = neg;
+            long long my = min(neg, W - neg);
+            for (int i = lo; i < hi; ++i) {
+                const int k = six[i];
+                if (lab[k] > 0) pp += wf[k]; else pn += wf[k];
+                long long e = -1;
+                if (i < J - 1 && sv[i + 1] > sv[i]) {
+                    e = pp + (neg - pn);
+                    my = min(my, min(e, W - e));
+                }
+                if (i < J - 1) errl[(size_t)f * J + i] = e;
+            }
+            emin = min(emin, my);
         }
-        __syncthreads();
-        if (tid == 0) {
-            double e = INFINITY;
-            for (int f = 0; f < nF; ++f) e = fmin(e, fmin_e[f]);
-            s_e = e;
-        }
-        __syncthreads();
-        const double lim = s_e + 1e-12;
-        // pass 2: first candidate within the tie tolerance, per feature
-        for (int f = wid; f < nF; f += nw) {
-            const double neg = s_neg[f];
-            long long cand = LLONG_MAX;
-            if (neg <= lim) cand = 0;
-            else if (W - neg <= lim) cand = 1;
+        emin = block_min_ll(emin, red_m);
+        const long long lim = emin + tol;
+        // pass 2: the first candidate (feature, threshold, polarity order) within the tolerance
+        long long chosen = LLONG_MAX;
+        int cf = -1;
+        for (int f = 0; f < nF && cf < 0; ++f) {
+            const long long neg = s_neg[f];
+            long long c = LLONG_MAX;
+            if (neg <= lim) c = 0;
+            else if (W - neg <= lim) c = 1;
             else {
-                for (int base = 0; base < J - 1 && cand == LLONG_MAX; base += 32) {
-                    const int i = base + lane;
-                    long long c = LLONG_MAX;
-                    if (i < J - 1) {
-                        const double e = err[(size_t)f * J + i];
-                        if (!isnan(e)) {
-                            if (e <= lim) c = 2 + 2LL * i;
-                            else if (W - e <= lim) c = 3 + 2LL * i;
-                        }
-                    }
-                    for (int off = 16; off > 0; off >>= 1) c = min(c, __shfl_down_sync(FULL, c, off));
-                    cand = __shfl_sync(FULL, c, 0);
+                for (int i = lo; i < hi && c == LLONG_MAX; ++i) {
+                    if (i >= J - 1) break;
+                    const long long e = errl[(size_t)f * J + i];
+                    if (e < 0) continue;
+                    if (e <= lim) c = 2 + 2LL * i;
+                    else if (W - e <= lim) c = 3 + 2LL * i;
                 }
             }
-            if (lane == 0) fcand[f] = cand;
+            c = block_min_ll(c, red_m);
+            if (c != LLONG_MAX) { chosen = c; cf = f; }
         }
-        __syncthreads();
         if (tid == 0) {
-            int f = 0;
-            while (f < nF && fcand[f] == LLONG_MAX) ++f;
-            if (f == nF) f = 0;   // cannot happen: the minimum is always a candidate
-            const long long c = fcand[f];
-            double e, th;
+            const int f = cf < 0 ? 0 : cf;
+            const long long c = cf < 0 ? 0 : chosen;
+            long long e;
+            double th;
             int pl;
             if (c < 2) {
                 th = -INFINITY;
@@ -648,11 +699,11 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
             } else {
                 const int i = (int)((c - 2) / 2);
                 pl = ((c - 2) % 2 == 0) ? 1 : -1;
-                const double ep = err[(size_t)f * J + i];
+                const long long ep = errl[(size_t)f * J + i];
                 e = pl > 0 ? ep : W - ep;
                 th = 0.5 * (sorted_v[(size_t)f * J + i] + sorted_v[(size_t)f * J + i + 1]);
             }
-            const double eps = e / W;
+            const double eps = (double)e / (double)W;
             s_stop = 0;
             if (eps >= 0.5 - 1e-12) {
                 s_stop = 1;
@@ -665,38 +716,32 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
                 pol[o_st + k] = pl;
                 alpha[o_st + k] = al;
                 s_f = f; s_thr = th; s_pol = pl; s_alpha = al;
+                s_fok = exp(-al);
+                s_fbad = exp(al);
                 if (eps <= 1e-10) s_stop = 2;
             }
         }
         __syncthreads();
         if (s_stop == 1) break;
-        // weight update w_i <- w_i exp(-alpha y_i h(x_i)), then normalise
+        // w_i <- w_i exp(-alpha y_i h(x_i)), then normalise
         {
             const int f = s_f;
-            const double th = s_thr, al = s_alpha;
+            const double th = s_thr, fok = s_fok, fbad = s_fbad;
             const int pl = s_pol;
-            double part2 = 0.0;
-            // h(x_i) through the sorted order of feature f, which holds the feature values
             const double* sv = sorted_v + (size_t)f * J;
-            const int* si = sorted_i + (size_t)f * J;
+            const int* six = sorted_i + (size_t)f * J;
+            double part2 = 0.0;
             for (int r = tid; r < J; r += blockDim.x) {
-                const int i = si[r];
-                const double h = sv[r] > th ? (double)pl : (double)-pl;
-                w[i] = w[i] * exp(-al * (double)label[i] * h);
+                const int i = six[r];
+                const int h = sv[r] > th ? pl : -pl;
+                const double nw = w[i] * (h == lab[i] ? fok : fbad);
+                w[i] = nw;
+                part2 += nw;
             }
             __syncthreads();
-            for (int i = tid; i < J; i += blockDim.x) part2 += w[i];
-            for (int off = 16; off > 0; off >>= 1) part2 += __shfl_down_sync(FULL, part2, off);
-            if (lane == 0) wred[wid] = part2;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int k = 0; k < nw; ++k) t += wred[k];
-                s_W = t;
-            }
-            __syncthreads();
-            const double Wn = s_W;
-            for (int i = tid; i < J; i += blockDim.x) w[i] = w[i] / Wn;
+            const double Wn = block_sum_d(part2, red_d);
+            const double inv = 1.0 / Wn;
+            for (int i = tid; i < J; i += blockDim.x) w[i] *= inv;
             __syncthreads();
         }
         if (s_stop == 2) break;
@@ -708,6 +753,23 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
                       rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
         fitted[m] = 1;
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// End of one Newton pass in a graph whose loop is a conditional while node: advance the
+// iterate index, clear the list the pass consumed (it receives the pass after next) and the
+// unit counter, and continue only while points remain and fewer than max_iter passes ran.
+
+__global__ void newton_decide_kernel(IterState* s, int max_iter, cudaGraphConditionalHandle h,
+                                     int* passes) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *passes += 1;
+    const int it = s->iter;
+    const int next_n = s->count[(it + 1) & 1];
+    s->count[it & 1] = 0;
+    s->work = 0ULL;
+    s->iter = it + 1;
+    cudaGraphSetConditional(h, (next_n > 0 && it + 1 < max_iter) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------

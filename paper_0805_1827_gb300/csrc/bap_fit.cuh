@@ -26,6 +26,8 @@ __global__ void adaboost_kernel(const DevModel* M, int m, int J, const double* X
                                 double* sorted_v, int* sorted_i, double* err, int max_stumps,
                                 int* n_stumps, int* feat, double* thr, int* pol, double* alpha,
                                 int rec_len, float* rec_f, double* rec_d, int* fitted);
+__global__ void newton_decide_kernel(IterState* s, int max_iter, cudaGraphConditionalHandle h,
+                                     int* passes);
 __global__ void set_int_kernel(int* p, int v);
 __global__ void copy_s0_kernel(const DevModel* M, double* start);
 __global__ void rng_debug_kernel(RoundKeys rk, uint32_t w1, uint32_t step, int d, long long count,

@@ -32,6 +32,15 @@ struct DevModel {
     double vol2[MAXDATES + 1][MAXD];       // sigma_q sqrt(t_k - t_{k-1}) / ln 2
 };
 
+// Iteration state of a Newton loop whose iterations are decided on the device: the iterate
+// index, the counts of the two ping-pong item lists and the unit counter of the next pass.
+struct IterState {
+    int iter;
+    int count[2];
+    int pad;
+    unsigned long long work;
+};
+
 // Newton state of one I&Z boundary point (FP64, Section 2.3 "Newton's iterations").
 struct ItemState {
     double x, lo, hi, dx_old, dx;

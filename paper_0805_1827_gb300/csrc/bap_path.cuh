@@ -59,6 +59,11 @@ struct PathArgs {
     ItemState* state;            // MODE_NEWTON
     int* next_active;
     int* next_count;
+    // Newton loop decided on the device: when iter_ptr is set, the item list, its count, the
+    // next list and its count are the ping-pong pair selected by the iterate index *iter_ptr
+    const int* iter_ptr;
+    int* list_pp[2];
+    int* count_pp;
     double f_tol, x_tol, fp_eps;
     int max_iter, fixed_point;
     double* label_y;             // MODE_LABEL: Phi - C
@@ -249,7 +254,18 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const long long total_units = (long long)(*a.n_active) * a.C;
+    const int* active = a.active;
+    const int* n_active = a.n_active;
+    int* next_active = a.next_active;
+    int* next_count = a.next_count;
+    if (a.iter_ptr) {
+        const int itv = *a.iter_ptr;
+        active = a.list_pp[itv & 1];
+        n_active = a.count_pp + (itv & 1);
+        next_active = a.list_pp[(itv + 1) & 1];
+        next_count = a.count_pp + ((itv + 1) & 1);
+    }
+    const long long total_units = (long long)(*n_active) * a.C;
     const Real K = (Real)a.K;
     const bool is_put = a.payoff == BAP_BASKET_PUT;
     const bool is_max = a.payoff == BAP_MAX_CALL;
@@ -272,7 +288,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
         if (unit >= total_units) break;
         const int slot = (int)(unit / a.C);
         const int chunk = (int)(unit - (long long)slot * a.C);
-        const int item = a.active ? a.active[slot] : slot;
+        const int item = active ? active[slot] : slot;
 
         // log2 of the start point in FP64, one coordinate per lane, then broadcast
         const double* st = a.start + (size_t)item * D;
@@ -520,8 +536,8 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             } else if (a.mode == MODE_NEWTON) {
                 const double x = a.state[item].x;
                 if (newton_update(a, item, t0 / Nd, t2 / (Nd * x))) {
-                    const int pos = atomicAdd(a.next_count, 1);
-                    a.next_active[pos] = item;
+                    const int pos = atomicAdd(next_count, 1);
+                    next_active[pos] = item;
                 }
             } else if (a.mode == MODE_LABEL) {
                 const double phi = payoff64(a, a.start + (size_t)item * D, D);

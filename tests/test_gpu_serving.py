@@ -1,0 +1,106 @@
+"""Launch forms and the serving loop (needs a CUDA device).
+
+* The I&Z fit as one CUDA graph (Newton loops as conditional while nodes) gives bitwise the same
+  fit and price as the plain form with one launch per Newton pass.
+* Served requests (continuous batching, overlapping on the device) give bitwise the same results
+  as the same requests run alone through the direct calls.
+"""
+import numpy as np
+import pytest
+
+import paper_0805_1827_gb300 as bap
+from bap_workloads import CMCParams, IZParams, serving_stream, spec_max_call, spec_put_1d
+
+pytestmark = pytest.mark.gpu
+
+
+def _fit(spec, params, mode):
+    o = bap.Option(spec)
+    o.set_launch_mode(mode)
+    if hasattr(params, "N1"):
+        o.fit_boundary(params)
+    else:
+        o.fit_classifier(params)
+    return o
+
+
+def test_graph_and_plain_launch_forms_agree():
+    spec = spec_max_call(3, 100.0, rho=0.2, n_dates=6, T=2.0)
+    params = IZParams(J=32, N1=4000, degree=2, seed=3)
+    a = _fit(spec, params, bap.LAUNCH_PLAIN)
+    b = _fit(spec, params, bap.LAUNCH_GRAPH)
+    for m in range(1, spec.n_dates):
+        xa, ia, sa = a.fit_points(m)
+        xb, ib, sb = b.fit_points(m)
+        assert np.array_equal(xa, xb) and np.array_equal(ia, ib) and np.array_equal(sa, sb), m
+    ra, rb = a.price(100_000, 5), b.price(100_000, 5)
+    assert ra["price"] == rb["price"] and ra["var"] == rb["var"]
+    assert ra["fit_path_steps"] == rb["fit_path_steps"]
+    # the graph runs only the Newton passes that are needed
+    assert rb["kernel_launches"] < ra["kernel_launches"]
+    assert rb["path_launches"] < ra["path_launches"]
+    # replay of the same graph, and a rebuild for new parameters
+    b.fit_boundary(params)
+    assert b.price(100_000, 5)["price"] == rb["price"]
+    p2 = IZParams(J=16, N1=2000, degree=1, seed=4)
+    b.fit_boundary(p2)
+    c = _fit(spec, p2, bap.LAUNCH_PLAIN)
+    assert b.price(50_000, 6)["price"] == c.price(50_000, 6)["price"]
+    for o in (a, b, c):
+        o.close()
+
+
+def _alone(req):
+    o = _fit(req.spec, req.params, bap.LAUNCH_GRAPH)
+    r = o.price(req.n_paths, req.seed)
+    o.close()
+    return r
+
+
+def test_served_results_equal_results_alone():
+    reqs = serving_stream(n=20, seed=3, budget_lo=2e3, budget_hi=3e4, n_price=20_000)
+    srv = bap.Server(device_mem_budget=4 << 30, max_inflight=6)
+    tickets = [srv.submit(r.spec, r.params, r.n_paths, r.seed) for r in reqs]
+    served = [srv.wait(t, 300.0) for t in tickets]
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    assert stats["peak_inflight"] > 1
+    for req, (st, res) in zip(reqs, served):
+        alone = _alone(req)
+        assert res["price"] == alone["price"], (req.method, req.spec.d, req.spec.payoff)
+        assert res["var"] == alone["var"]
+        assert res["fit_path_steps"] == alone["fit_path_steps"]
+        assert res["latency_ms"] >= res["queue_ms"] >= 0.0
+
+
+def test_server_admission_and_errors():
+    srv = bap.Server(device_mem_budget=1 << 20, max_inflight=2)
+    big = spec_max_call(5, 100.0, rho=0.3)
+    with pytest.raises(bap.BapError) as e:
+        srv.submit(big, IZParams(J=1024, N1=100_000), 1_000_000, 1)
+    assert e.value.status == bap.BAP_EBUSY
+    with pytest.raises(bap.BapError) as e:
+        srv.submit(big, IZParams(J=0, N1=100), 1000, 1)
+    assert e.value.status == bap.BAP_EINVAL
+    with pytest.raises(bap.BapError) as e:
+        srv.poll(12345)
+    assert e.value.status == bap.BAP_EINVAL
+    t = srv.submit(spec_put_1d(n_dates=4), IZParams(J=4, N1=256, degree=0, seed=1), 1000, 2)
+    st, res = srv.wait(t, 60.0)
+    assert st in (bap.BAP_OK, bap.BAP_ENOCONV) and res["price"] > 0
+    with pytest.raises(bap.BapError):
+        srv.poll(t)          # collected tickets are gone
+    srv.close()
+
+
+def test_server_cmc_and_mixed_memory_pressure():
+    """A budget that fits about one request at a time still completes everything in order."""
+    reqs = serving_stream(n=6, seed=7, budget_lo=2e3, budget_hi=1e4, n_price=10_000)
+    srv = bap.Server(device_mem_budget=64 << 20, max_inflight=4)
+    tickets = [srv.submit(r.spec, r.params, r.n_paths, r.seed) for r in reqs]
+    for req, t in zip(reqs, tickets):
+        st, res = srv.wait(t, 300.0)
+        assert res["price"] == _alone(req)["price"]
+    assert srv.stats()["peak_bytes"] <= 64 << 20 or srv.stats()["peak_inflight"] == 1
+    srv.close()
