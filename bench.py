@@ -249,7 +249,9 @@ def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
                         "4..50 dates, inner budget log-U[1e4,1e6], mixed payoffs, I&Z/CMC 50/50, "
                         "pricing 1e5 paths",
             "served": {**summary(list(lat.values()), span_srv), "max_inflight": max_inflight,
-                       "peak_inflight": stats["peak_inflight"]},
+                       "peak_inflight": stats["peak_inflight"],
+                       "server_thread_start_s": stats["start_ms"] / 1e3,
+                       "server_thread_finish_s": stats["finish_ms"] / 1e3},
             "plain_per_request": summary(list(lat_p.values()), span_plain),
             "results_equal": mismatches == 0, "mismatches": mismatches,
             "path_steps": steps}

@@ -129,6 +129,11 @@ typedef struct bap_server_stats {
     int64_t queued;           /* waiting for admission now */
     int64_t bytes_in_use;     /* estimated device memory of the requests in flight now */
     int64_t peak_bytes, peak_inflight;
+    double start_ms;          /* server-thread host time spent starting requests, of which: */
+    double load_ms;           /*   giving an option slot its model */
+    double fit_enqueue_ms;    /*   enqueueing fits (for I&Z including building the graph) */
+    double price_enqueue_ms;  /*   enqueueing pricing */
+    double finish_ms;         /* server-thread host time spent finishing requests */
 } bap_server_stats;
 
 typedef struct bap_option bap_option;
@@ -150,7 +155,10 @@ bap_status bap_set_profiling(bap_option *opt, int on);
  * node whose body runs one Newton pass and then a one-thread kernel that continues the loop only
  * while points remain unconverged (at most max_iter passes), so the loop costs no host round
  * trip and no empty launches.  0: plain form, one launch per Newton pass up to max_iter per date
- * (also used while profiling is on).  If the graph cannot be built, the plain form is used. */
+ * (also used while profiling is on).  If the graph cannot be built, the plain form is used.
+ * 2: one cooperative launch per date runs all its Newton passes, a grid-wide barrier between
+ * passes; the barrier's wait is bounded, and a barrier that times out makes the fit return
+ * ECUDA.  All three forms give bitwise the same fit.  Errors: EINVAL (mode outside 0..2). */
 bap_status bap_set_launch_mode(bap_option *opt, int mode);
 
 /* Ibanez-Zapatero fit (Algorithm 1 without [mc]): for m = N_T-1..1, boundary points by
@@ -234,7 +242,10 @@ bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_
 /* Errors: EINVAL (budget < 1 MiB, max_inflight outside 1..1024), ECUDA (no device), ENOMEM. */
 bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_server **out);
 
-/* Launch form of the I&Z fits the server runs (see bap_set_launch_mode; default 1). */
+/* Launch form of the I&Z fits the server runs (see bap_set_launch_mode).  Default 2 (one
+ * cooperative launch per date, on at most 1/min(max_inflight, 8) of the device): each request
+ * builds its fit once, so a graph's build and release cost more host time than its launches
+ * save, and the plain form's max_iter launches per date fill the stream's launch queue. */
 bap_status bap_server_set_launch_mode(bap_server *srv, int mode);
 
 /* Queue a request: method BAP_METHOD_IZ with params -> bap_iz_params, or BAP_METHOD_CMC with

@@ -28,7 +28,7 @@ EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch
             "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
             "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait",
             "bap_server_get_stats", "bap_server_destroy"]
-LAUNCH_PLAIN, LAUNCH_GRAPH = 0, 1
+LAUNCH_PLAIN, LAUNCH_GRAPH, LAUNCH_COOP = 0, 1, 2
 METHOD_CODE = {"iz": 0, "cmc": 1}
 
 
@@ -69,7 +69,9 @@ class _Result(C.Structure):
 class _ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("queued", C.c_int64), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
-                ("peak_inflight", C.c_int64)]
+                ("peak_inflight", C.c_int64), ("start_ms", C.c_double), ("load_ms", C.c_double),
+                ("fit_enqueue_ms", C.c_double), ("price_enqueue_ms", C.c_double),
+                ("finish_ms", C.c_double)]
 
 
 _lib = None

@@ -83,6 +83,8 @@ constexpr int kBlock = 256;
 struct FnInfo {
     int blocks_per_sm = 0;
     size_t smem_set = 0;
+    size_t occ_smem = ~size_t(0);   // shared-memory size of the cached occupancy query
+    int occ_blocks = 0;
 };
 std::mutex g_fn_mu;
 std::unordered_map<const void*, FnInfo> g_fn;
@@ -142,11 +144,18 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
             CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
             fi.smem_set = std::max<size_t>(smem, 48 * 1024);
         }
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
+        if (fi.occ_smem != smem) {
+            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fi.occ_blocks, fn, kBlock, smem));
+            fi.occ_smem = smem;
+        }
+        bps = fi.occ_blocks;
     }
     if (bps < 1) bps = 1;
     long long blocks = (max_units + (kBlock / 32) - 1) / (kBlock / 32);
-    blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
+    long long cap = (long long)o->sm_count * bps;
+    const bool coop = rule == R_NEWTON_COOP;
+    if (coop) cap = std::max(1LL, cap / std::max(1, o->grid_share));
+    blocks = std::max(1LL, std::min(blocks, cap));
     void* args[] = {&a};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = o->profiling && !fp64 && !o->capturing;
@@ -161,7 +170,10 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
         o->prof_used += 2;
         CU(cudaEventRecord(e0, o->stream));
     }
-    CU(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
+    if (coop)
+        CU(cudaLaunchCooperativeKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
+    else
+        CU(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
     if (timed) CU(cudaEventRecord(e1, o->stream));
     ++o->launches;
     ++o->path_launches;
@@ -193,12 +205,9 @@ void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
     for (int q = 0; q < d; ++q) {
         for (int j = 0; j <= q; ++j) {
             const double l = o->hm.L[q * MAXD + j];
-            const double v = a.uniform ? o->hm.vol2[1][q] * l : l;
-            a.Lf[q * MAXD + j] = (float)v;
-            a.Ld[q * MAXD + j] = v;
+            a.Lf[q * (q + 1) / 2 + j] = (float)(a.uniform ? o->hm.vol2[1][q] * l : l);
         }
         a.driftf[q] = (float)o->hm.drift2[1][q];
-        a.driftd[q] = o->hm.drift2[1][q];
         a.wf[q] = (float)o->hm.w[q];
     }
     a.total_steps = o->total_steps.as<unsigned long long>();
@@ -302,9 +311,8 @@ bap_status record_diag(bap_option* o, int m, bool iz) {
     return BAP_OK;
 }
 
-// One Newton pass of date m.  Plain form: iterate `it` uses the explicit ping-pong lists and
-// its own count and unit counter.  Device-decided form (it < 0): the kernel selects them from
-// the iteration state, which newton_decide_kernel advances.
+// One Newton pass of date m: pass `it` (plain form), or the pass that the iteration state names
+// (it < 0: graph form, advanced by newton_decide_kernel).
 bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int it, int chunk,
                                int C) {
     PathArgs a;
@@ -313,21 +321,12 @@ bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int
     a.N = p->N1;
     a.chunk = chunk;
     a.C = C;
-    if (it >= 0) {
-        a.active = (it & 1) ? o->active1.as<int>() : o->active0.as<int>();
-        a.n_active = o->counts.as<int>() + it;
-        a.work = o->work.as<unsigned long long>() + it;
-        a.next_active = (it & 1) ? o->active0.as<int>() : o->active1.as<int>();
-        a.next_count = o->counts.as<int>() + it + 1;
-    } else {
-        IterState* is = o->iterstate.as<IterState>();
-        a.iter_ptr = &is->iter;
-        a.list_pp[0] = o->active0.as<int>();
-        a.list_pp[1] = o->active1.as<int>();
-        a.count_pp = is->count;
-        a.work = &is->work;
-        a.n_active = is->count;     // unused when iter_ptr is set
-    }
+    a.list[0] = o->active0.as<int>();
+    a.list[1] = o->active1.as<int>();
+    a.count = o->counts.as<int>();
+    a.work = o->work.as<unsigned long long>();
+    if (it >= 0) a.pass_it = it;
+    else a.iter_ptr = &o->iterstate.as<IterState>()->iter;
     a.start = o->start.as<double>();
     a.ctr_item = o->ctr_item.as<int>();
     a.pivot = o->pivot.as<int>();
@@ -341,6 +340,41 @@ bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int
     a.max_iter = p->max_iter;
     a.fixed_point = p->fixed_point;
     return launch_path(o, a, R_IZ, false, (long long)o->n_items * C);
+}
+
+// All Newton passes of date m in one cooperative launch (newton_coop_kernel), on the per-pass
+// lists, counts and unit counters of the plain form; the grid barrier's counter is the last
+// count slot (index max_iter + 1, which no pass writes) and its failure flag stat_counts[3].
+bap_status enqueue_newton_coop(bap_option* o, const bap_iz_params* p, int m, int chunk, int C) {
+    PathArgs a;
+    base_args(o, a, m, MODE_NEWTON, false);
+    a.rk = make_round_keys(p->seed, P_IZ, (uint32_t)m);
+    a.N = p->N1;
+    a.chunk = chunk;
+    a.C = C;
+    a.list[0] = o->active0.as<int>();
+    a.list[1] = o->active1.as<int>();
+    a.count = o->counts.as<int>();
+    a.work = o->work.as<unsigned long long>();
+    a.passes = o->stat_counts.as<int>() + 2;
+    a.coop_bar = reinterpret_cast<unsigned*>(o->counts.as<int>() + p->max_iter + 1);
+    a.coop_err = o->stat_counts.as<int>() + 3;
+    // a wait at the barrier never lasts longer than a pass: allow 5 s plus 1 ns per path step
+    a.coop_limit_ns = 5000000000ULL + (unsigned long long)o->n_items *
+                                          (unsigned long long)p->N1 * (unsigned long long)(o->n_dates - m);
+    a.start = o->start.as<double>();
+    a.ctr_item = o->ctr_item.as<int>();
+    a.pivot = o->pivot.as<int>();
+    a.partial = o->partial.as<double>();
+    a.partial_steps = o->partial_steps.as<long long>();
+    a.done = o->done.as<int>();
+    a.state = o->state.as<ItemState>();
+    a.f_tol = p->f_tol;
+    a.x_tol = p->x_tol;
+    a.fp_eps = p->fp_eps;
+    a.max_iter = p->max_iter;
+    a.fixed_point = p->fixed_point;
+    return launch_path(o, a, R_NEWTON_COOP, false, (long long)o->n_items * C);
 }
 
 bap_status enqueue_iz_prologue(bap_option* o, const bap_iz_params* p) {
@@ -367,15 +401,10 @@ bap_status enqueue_iz_prologue(bap_option* o, const bap_iz_params* p) {
 
 bap_status enqueue_iz_setup(bap_option* o, const bap_iz_params* p, int m, bool device_loop) {
     cudaStream_t st = o->stream;
-    int* count0;
-    if (device_loop) {
-        CU(cudaMemsetAsync(o->iterstate.p, 0, sizeof(IterState), st));
-        count0 = o->iterstate.as<IterState>()->count;
-    } else {
-        CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
-        CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
-        count0 = o->counts.as<int>();
-    }
+    if (device_loop) CU(cudaMemsetAsync(o->iterstate.p, 0, sizeof(IterState), st));
+    CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
+    CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
+    int* count0 = o->counts.as<int>();
     iz_setup_kernel<<<(o->n_items + 127) / 128, 128, 0, st>>>(
         o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
         o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), count0);
@@ -441,8 +470,8 @@ bap_status build_iz_graph(bap_option* o, const bap_iz_params* p, int chunk, int 
         if (e != cudaSuccess) { status = fail(BAP_ECUDA, "capture: %s", cudaGetErrorString(e)); break; }
         status = enqueue_newton_pass(o, p, m, -1, chunk, C);
         if (status == BAP_OK) {
-            newton_decide_kernel<<<1, 32, 0, st>>>(o->iterstate.as<IterState>(), p->max_iter, h,
-                                                   o->stat_counts.as<int>() + 2);
+            newton_decide_kernel<<<1, 32, 0, st>>>(o->iterstate.as<IterState>(), o->counts.as<int>(),
+                                                   p->max_iter, h, o->stat_counts.as<int>() + 2);
             ++o->launches;
             if (cudaGetLastError() != cudaSuccess) status = fail(BAP_ECUDA, "decide kernel");
         }
@@ -504,8 +533,7 @@ bap_status run_sums_enqueue(bap_option* o, int m, int mode, bool fp64, const Rou
     a.N = N;
     a.chunk = chunk;
     a.C = C;
-    a.active = nullptr;
-    a.n_active = o->counts.as<int>();
+    a.count = o->counts.as<int>();
     a.work = o->work.as<unsigned long long>();
     a.start = d_start;
     a.ctr_item = d_item_ids;
@@ -541,9 +569,11 @@ bap_status run_sums(bap_option* o, int m, int mode, bool fp64, const RoundKeys& 
 
 namespace bap {
 
-bap_status option_create(const bap_model* md, bap_option** out) {
+// Validated model and its FP64 set-up: the lower Cholesky factor of rho (the positive
+// definiteness check) and the per-date stepping constants in log2 units.  A few hundred flops
+// per option, done once on the host so that creating an option never waits for the device.
+bap_status model_prepare(const bap_model* md, DevModel* out) {
     if (!md || !out) return fail(BAP_EINVAL, "null argument");
-    *out = nullptr;
     const int d = md->d;
     if (d < 1 || d > BAP_MAX_D) return fail(BAP_EINVAL, "d=%d outside 1..%d", d, BAP_MAX_D);
     if (!md->S0 || !md->sigma || !md->delta || !md->rho) return fail(BAP_EINVAL, "null model array");
@@ -583,63 +613,112 @@ bap_status option_create(const bap_model* md, bap_option** out) {
     }
     if (std::fabs(hm.t[md->n_dates] - md->T) > 1e-12 * md->T) return fail(BAP_EINVAL, "last date must equal T");
     hm.t[md->n_dates] = md->T;
+    // Cholesky rho = L L^T (lower, FP64)
+    for (int j = 0; j < d; ++j) {
+        double sjj = md->rho[j * d + j];
+        for (int k = 0; k < j; ++k) sjj -= hm.L[j * MAXD + k] * hm.L[j * MAXD + k];
+        if (!(sjj > 1e-14)) return fail(BAP_EINVAL, "rho is not positive definite");
+        const double ljj = std::sqrt(sjj);
+        hm.L[j * MAXD + j] = ljj;
+        for (int i = j + 1; i < d; ++i) {
+            double v = md->rho[i * d + j];
+            for (int k = 0; k < j; ++k) v -= hm.L[i * MAXD + k] * hm.L[j * MAXD + k];
+            hm.L[i * MAXD + j] = v / ljj;
+        }
+    }
+    const double inv_ln2 = 1.4426950408889634;
+    int uniform = 1;
+    const double dt1 = hm.t[1] - hm.t[0];
+    for (int k = 1; k <= hm.n_dates; ++k) {
+        const double dt = hm.t[k] - hm.t[k - 1];
+        if (std::fabs(dt - dt1) > 1e-12 * hm.t[hm.n_dates]) uniform = 0;
+        for (int q = 0; q < d; ++q) {
+            hm.drift2[k][q] = (hm.r - hm.delta[q] - 0.5 * hm.sigma[q] * hm.sigma[q]) * dt * inv_ln2;
+            hm.vol2[k][q] = hm.sigma[q] * std::sqrt(dt) * inv_ln2;
+        }
+    }
+    hm.uniform_dates = uniform;
+    *out = hm;
+    return BAP_OK;
+}
 
+// Stream, events and page-locked results of an option, without a model yet.
+bap_status option_alloc(bap_option** out) {
+    *out = nullptr;
     int dev;
     if (!has_device(&dev)) return fail(BAP_ECUDA, "no CUDA device");
     bap_option* o = new (std::nothrow) bap_option();
     if (!o) return fail(BAP_ENOMEM, "host allocation");
     o->device = dev;
-    o->d = d;
-    o->n_dates = md->n_dates;
-    o->payoff = md->payoff;
-    o->r = md->r;
-    o->K = md->K;
-    o->T = md->T;
-    // temporaries of the set-up; released before the option (and its stream) on every path
-    DevBuf drho, dstatus;
-    auto cleanup = [&](bap_status s) {
-        drho.release(o->stream);
-        dstatus.release(o->stream);
-        option_destroy(o);
-        return s;
-    };
     keep_pool_cached(dev);
     cudaError_t e = cudaDeviceGetAttribute(&o->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
-    e = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&o->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        option_destroy(o);
+        return fail(BAP_ECUDA, "%s", cudaGetErrorString(e));
+    }
     o->stream = o->own_stream;
-    AllocScope scope(o->stream);
     if (cudaEventCreate(&o->ev0) != cudaSuccess || cudaEventCreate(&o->ev1) != cudaSuccess ||
-        cudaEventCreate(&o->ev2) != cudaSuccess || cudaEventCreate(&o->ev3) != cudaSuccess)
-        return cleanup(fail(BAP_ECUDA, "event create"));
+        cudaEventCreate(&o->ev2) != cudaSuccess || cudaEventCreate(&o->ev3) != cudaSuccess) {
+        option_destroy(o);
+        return fail(BAP_ECUDA, "event create");
+    }
     o->pin = pinned_get();
-    if (!o->pin) return cleanup(fail(BAP_ENOMEM, "page-locked host allocation"));
+    if (!o->pin) {
+        option_destroy(o);
+        return fail(BAP_ENOMEM, "page-locked host allocation");
+    }
     memset(o->pin, 0, sizeof(PinnedOut));
-    bap_status st;
-    if ((st = o->dmodel.reserve(sizeof(DevModel))) != BAP_OK) return cleanup(st);
-    if ((st = o->s0buf.reserve((size_t)d * 8)) != BAP_OK) return cleanup(st);
-    if ((st = o->fitted.reserve((md->n_dates + 1) * sizeof(int))) != BAP_OK) return cleanup(st);
-    if ((st = o->total_steps.reserve(8)) != BAP_OK) return cleanup(st);
-    if ((st = o->stat_counts.reserve(16)) != BAP_OK) return cleanup(st);
-    if ((st = o->one.reserve(8)) != BAP_OK) return cleanup(st);
-    if ((st = drho.reserve((size_t)d * d * 8)) != BAP_OK) return cleanup(st);
-    if ((st = dstatus.reserve(4)) != BAP_OK) return cleanup(st);
-    e = cudaMemcpyAsync(o->dmodel.p, &hm, sizeof hm, cudaMemcpyHostToDevice, o->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(drho.p, md->rho, (size_t)d * d * 8, cudaMemcpyHostToDevice, o->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(o->fitted.p, 0, (md->n_dates + 1) * sizeof(int), o->stream);
-    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
-    model_setup_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), drho.as<double>(), dstatus.as<int>());
-    copy_s0_kernel<<<1, 32, 0, o->stream>>>(o->dmodel.as<DevModel>(), o->s0buf.as<double>());
-    int status = -1;
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&o->hm, o->dmodel.p, sizeof(DevModel), cudaMemcpyDeviceToHost, o->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, dstatus.p, 4, cudaMemcpyDeviceToHost, o->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(o->stream);
-    if (e != cudaSuccess) return cleanup(fail(BAP_ECUDA, "%s", cudaGetErrorString(e)));
-    if (status != 0) return cleanup(fail(BAP_EINVAL, "rho is not positive definite"));
-    drho.release(o->stream);
-    dstatus.release(o->stream);
+    *out = o;
+    return BAP_OK;
+}
+
+// Gives an idle option a (prepared) model: uploads it and clears the fitted rule.
+bap_status option_load(bap_option* o, const DevModel& hm) {
+    AllocScope scope(o->stream);
+    o->d = hm.d;
+    o->n_dates = hm.n_dates;
+    o->payoff = hm.payoff;
+    o->r = hm.r;
+    o->K = hm.K;
+    o->T = hm.t[hm.n_dates];
+    o->hm = hm;
+    o->rule_kind = R_NONE;
+    o->method = -1;
+    o->n_items = 0;
+    o->last_noconv = o->last_noroot = 0;
+    o->last_fit_steps = 0;
+    o->last_fit_ms = 0;
+    o->fit_launches = o->fit_path_launches = 0;
+    o->fit_path_ms = 0;
+    if (o->graph_exec) {
+        cudaGraphExecDestroy(o->graph_exec);
+        o->graph_exec = nullptr;
+    }
+    TRY(o->dmodel.reserve(sizeof(DevModel)));
+    TRY(o->s0buf.reserve((size_t)MAXD * 8));
+    TRY(o->fitted.reserve((MAXDATES + 1) * sizeof(int)));
+    TRY(o->total_steps.reserve(8));
+    TRY(o->stat_counts.reserve(16));
+    TRY(o->one.reserve(8));
+    CU(cudaMemcpyAsync(o->dmodel.p, &o->hm, sizeof(DevModel), cudaMemcpyHostToDevice, o->stream));
+    CU(cudaMemcpyAsync(o->s0buf.p, o->hm.S0, (size_t)hm.d * 8, cudaMemcpyHostToDevice, o->stream));
+    CU(cudaMemsetAsync(o->fitted.p, 0, (hm.n_dates + 1) * sizeof(int), o->stream));
+    return BAP_OK;
+}
+
+bap_status option_create(const bap_model* md, bap_option** out) {
+    if (!out) return fail(BAP_EINVAL, "null argument");
+    *out = nullptr;
+    DevModel hm;
+    TRY(model_prepare(md, &hm));
+    bap_option* o;
+    TRY(option_alloc(&o));
+    const bap_status st = option_load(o, hm);
+    if (st != BAP_OK) {
+        option_destroy(o);
+        return st;
+    }
     *out = o;
     return BAP_OK;
 }
@@ -740,7 +819,10 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
         TRY(enqueue_iz_prologue(o, p));
         for (int m = o->n_dates - 1; m >= 1; --m) {
             TRY(enqueue_iz_setup(o, p, m, false));
-            for (int it = 0; it < p->max_iter; ++it) TRY(enqueue_newton_pass(o, p, m, it, chunk, C));
+            if (o->launch_mode == LAUNCH_COOP && !o->profiling)
+                TRY(enqueue_newton_coop(o, p, m, chunk, C));
+            else
+                for (int it = 0; it < p->max_iter; ++it) TRY(enqueue_newton_pass(o, p, m, it, chunk, C));
             TRY(enqueue_iz_fit_date_end(o, p, m));
         }
     }
@@ -757,6 +839,8 @@ bap_status finish_fit_iz(bap_option* o) {
     o->last_fit_steps = (long long)o->pin->fit_steps;
     o->last_noconv = o->pin->counts[0];
     o->last_noroot = o->pin->counts[1];
+    if (o->pin->counts[3] != 0)
+        return fail(BAP_ECUDA, "Newton loop: a grid barrier of the cooperative launch timed out");
     if (o->last_graph) {
         o->launches += 2LL * o->pin->counts[2];
         o->path_launches += o->pin->counts[2];
@@ -820,8 +904,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         a.N = p->N2;
         a.chunk = chunk;
         a.C = C;
-        a.active = nullptr;
-        a.n_active = o->counts.as<int>();
+        a.count = o->counts.as<int>();
         a.work = o->work.as<unsigned long long>();
         a.start = o->start.as<double>();
         a.ctr_item = o->ctr_item.as<int>();
@@ -962,7 +1045,8 @@ bap_status bap_set_profiling(bap_option* o, int on) {
 
 bap_status bap_set_launch_mode(bap_option* o, int mode) {
     if (!o) return fail(BAP_EINVAL, "null option");
-    if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH) return fail(BAP_EINVAL, "bad launch mode");
+    if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH && mode != LAUNCH_COOP)
+        return fail(BAP_EINVAL, "bad launch mode");
     o->launch_mode = mode;
     return BAP_OK;
 }
@@ -1283,8 +1367,7 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     a.N = N;
     a.chunk = chunk;
     a.C = (int)C;
-    a.active = nullptr;
-    a.n_active = reinterpret_cast<const int*>(base + 16);
+    a.count = reinterpret_cast<int*>(base + 16);
     a.work = reinterpret_cast<unsigned long long*>(base);
     a.total_steps = reinterpret_cast<unsigned long long*>(base + 8);
     a.start = const_cast<double*>(d_starts);

@@ -8,42 +8,6 @@
 namespace bap {
 
 // ---------------------------------------------------------------------------------------------
-// Model set-up: FP64 Cholesky factor of rho and the per-date stepping constants (log2 units).
-// status: 0 ok, 1 rho not positive definite.
-
-__global__ void model_setup_kernel(DevModel* M, const double* rho, int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int d = M->d;
-    for (int i = 0; i < MAXD * MAXD; ++i) M->L[i] = 0.0;
-    int ok = 1;
-    for (int j = 0; j < d && ok; ++j) {
-        double s = rho[j * d + j];
-        for (int k = 0; k < j; ++k) s -= M->L[j * MAXD + k] * M->L[j * MAXD + k];
-        if (!(s > 1e-14)) { ok = 0; break; }
-        const double ljj = sqrt(s);
-        M->L[j * MAXD + j] = ljj;
-        for (int i = j + 1; i < d; ++i) {
-            double v = rho[i * d + j];
-            for (int k = 0; k < j; ++k) v -= M->L[i * MAXD + k] * M->L[j * MAXD + k];
-            M->L[i * MAXD + j] = v / ljj;
-        }
-    }
-    const double inv_ln2 = 1.4426950408889634;
-    int uniform = 1;
-    const double dt1 = M->t[1] - M->t[0];
-    for (int k = 1; k <= M->n_dates; ++k) {
-        const double dt = M->t[k] - M->t[k - 1];
-        if (fabs(dt - dt1) > 1e-12 * M->t[M->n_dates]) uniform = 0;
-        for (int q = 0; q < d; ++q) {
-            M->drift2[k][q] = (M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q]) * dt * inv_ln2;
-            M->vol2[k][q] = M->sigma[q] * sqrt(dt) * inv_ln2;
-        }
-    }
-    M->uniform_dates = uniform;
-    *status = ok ? 0 : 1;
-}
-
-// ---------------------------------------------------------------------------------------------
 // [glp] Korobov rank-1 lattice (Section 2.3): the multiplier a minimising the P_2 figure of
 // merit -1 + (1/J) sum_j prod_k (1 + 2 pi^2 B_2({j a^k / J})), B_2(x) = x^2 - x + 1/6, over
 // a in [1, J) coprime to J; ties within 1e-9 (relative) go to the smallest a.
@@ -756,18 +720,16 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
 }
 
 // ---------------------------------------------------------------------------------------------
-// End of one Newton pass in a graph whose loop is a conditional while node: advance the
-// iterate index, clear the list the pass consumed (it receives the pass after next) and the
-// unit counter, and continue only while points remain and fewer than max_iter passes ran.
+// End of one Newton pass in a graph whose loop is a conditional while node: advance the pass
+// index, and continue only while points remain and fewer than max_iter passes ran (each pass has
+// its own count and unit counter, zeroed at the date's set-up).
 
-__global__ void newton_decide_kernel(IterState* s, int max_iter, cudaGraphConditionalHandle h,
-                                     int* passes) {
+__global__ void newton_decide_kernel(IterState* s, const int* count, int max_iter,
+                                     cudaGraphConditionalHandle h, int* passes) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     *passes += 1;
     const int it = s->iter;
-    const int next_n = s->count[(it + 1) & 1];
-    s->count[it & 1] = 0;
-    s->work = 0ULL;
+    const int next_n = count[it + 1];
     s->iter = it + 1;
     cudaGraphSetConditional(h, (next_n > 0 && it + 1 < max_iter) ? 1u : 0u);
 }
@@ -777,11 +739,6 @@ __global__ void newton_decide_kernel(IterState* s, int max_iter, cudaGraphCondit
 
 __global__ void set_int_kernel(int* p, int v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
-}
-
-__global__ void copy_s0_kernel(const DevModel* M, double* start) {
-    const int q = threadIdx.x;
-    if (q < M->d) start[q] = M->S0[q];
 }
 
 __global__ void rng_debug_kernel(RoundKeys rk, uint32_t w1, uint32_t step, int d, long long count,

@@ -5,7 +5,6 @@
 
 namespace bap {
 
-__global__ void model_setup_kernel(DevModel* M, const double* rho, int* status);
 __global__ void korobov_merit_kernel(int J, int s, double* merit);
 __global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_a);
 __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
@@ -26,10 +25,9 @@ __global__ void adaboost_kernel(const DevModel* M, int m, int J, const double* X
                                 double* sorted_v, int* sorted_i, double* err, int max_stumps,
                                 int* n_stumps, int* feat, double* thr, int* pol, double* alpha,
                                 int rec_len, float* rec_f, double* rec_d, int* fitted);
-__global__ void newton_decide_kernel(IterState* s, int max_iter, cudaGraphConditionalHandle h,
-                                     int* passes);
+__global__ void newton_decide_kernel(IterState* s, const int* count, int max_iter,
+                                     cudaGraphConditionalHandle h, int* passes);
 __global__ void set_int_kernel(int* p, int v);
-__global__ void copy_s0_kernel(const DevModel* M, double* start);
 __global__ void rng_debug_kernel(RoundKeys rk, uint32_t w1, uint32_t step, int d, long long count,
                                  uint32_t* words, double* z);
 __global__ void collect_points_kernel(const ItemState* state, int n, double* x_out, int* it_out,

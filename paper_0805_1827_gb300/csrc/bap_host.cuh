@@ -87,7 +87,9 @@ struct PinnedOut {
     long long steps64;
 };
 
-enum LaunchMode : int { LAUNCH_PLAIN = 0, LAUNCH_GRAPH = 1 };
+// Launch form of the I&Z Newton passes: one launch per pass (max_iter per date), one graph for
+// the whole fit (conditional while node per date), or one cooperative launch per date.
+enum LaunchMode : int { LAUNCH_PLAIN = 0, LAUNCH_GRAPH = 1, LAUNCH_COOP = 2 };
 
 // Page-locked result blocks come from a slab that is never freed (cudaFreeHost would wait for
 // the whole device).
@@ -136,6 +138,7 @@ struct bap_option {
     size_t prof_used = 0;
     // graph of the I&Z fit (Newton loops as conditional while nodes)
     int launch_mode = bap::LAUNCH_GRAPH;
+    int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device
     cudaGraphExec_t graph_exec = nullptr;
     bap_iz_params graph_params{};
     int graph_failed = 0;
@@ -155,6 +158,9 @@ struct bap_option {
 
 namespace bap {
 
+bap_status model_prepare(const bap_model* md, DevModel* out);
+bap_status option_alloc(bap_option** out);
+bap_status option_load(bap_option* o, const DevModel& hm);
 bap_status option_create(const bap_model* md, bap_option** out);
 void option_destroy(bap_option* o);
 bap_status validate_iz(const bap_option* o, const bap_iz_params* p);

@@ -17,6 +17,8 @@ constexpr int WARP = 32;
 
 enum Purpose : uint32_t { P_IZ = 1, P_CMC = 2, P_TRAIN = 3, P_PRICE = 4 };
 enum RuleKind : int { R_NONE = 0, R_IZ = 1, R_CMC = 2 };
+// Kernel selector (not a rule kind): the cooperative kernel that runs all Newton passes of a date.
+constexpr int R_NEWTON_COOP = 3;
 enum Mode : int { MODE_SUMS = 0, MODE_NEWTON = 1, MODE_LABEL = 2, MODE_TRACE = 3 };
 enum ItemStatus : int { ST_OK = 0, ST_NOCONV = 1, ST_NOROOT = 2 };
 
@@ -32,13 +34,11 @@ struct DevModel {
     double vol2[MAXDATES + 1][MAXD];       // sigma_q sqrt(t_k - t_{k-1}) / ln 2
 };
 
-// Iteration state of a Newton loop whose iterations are decided on the device: the iterate
-// index, the counts of the two ping-pong item lists and the unit counter of the next pass.
+// Iteration state of a Newton loop whose passes are decided on the device: the index of the
+// next pass.
 struct IterState {
     int iter;
-    int count[2];
-    int pad;
-    unsigned long long work;
+    int pad[3];
 };
 
 // Newton state of one I&Z boundary point (FP64, Section 2.3 "Newton's iterations").

@@ -26,18 +26,24 @@ struct PathArgs {
     int mode;                    // Mode
     int n_dates, payoff, uniform;
     double r, K;
-    float Lf[MAXD * MAXD];       // vol-scaled Cholesky factor (uniform dates) or plain L
-    double Ld[MAXD * MAXD];
-    float driftf[MAXD];          // uniform dates: per-step log2 drift
-    double driftd[MAXD];
+    float Lf[MAXD * (MAXD + 1) / 2];   // packed lower Cholesky factor, row q at q(q+1)/2,
+                                       // vol-scaled for uniform dates (FP32 kernels)
+    float driftf[MAXD];          // uniform dates: per-step log2 drift (FP32 kernels)
     float wf[MAXD];              // basket / geometric weights
     RoundKeys rk;
     int64_t N;                   // paths per item
     int chunk;                   // paths per unit (multiple of 32)
     int C;                       // units per item
-    const int* active;           // item list (nullptr: item = slot)
-    const int* n_active;         // device count of the list
-    unsigned long long* work;    // unit counter (zeroed before the launch)
+    // Item lists of the passes.  Pass `it` works on the count[it] items list[it & 1][0..) (items
+    // 0, 1, ... when that list is null), taking units from the counter work[it]; the Newton
+    // epilogue appends the items that go on to list[(it + 1) & 1] at count[it + 1].  Counts and
+    // counters are zero before their pass.  `it` is pass_it, or *iter_ptr when iter_ptr is set
+    // (graph form), or the pass loop index of the cooperative kernel.
+    int* list[2];
+    int* count;
+    unsigned long long* work;
+    int pass_it;
+    const int* iter_ptr;
     double* start;               // items x d start points (FP64); Newton writes the pivot value
     const int* ctr_item;         // Philox counter word 1 per item (nullptr: 0)
     const int* pivot;            // pivot asset per item for the pathwise derivative (or nullptr)
@@ -57,13 +63,12 @@ struct PathArgs {
     int* trace_tau;              // MODE_TRACE: per path
     double* trace_phi;
     ItemState* state;            // MODE_NEWTON
-    int* next_active;
-    int* next_count;
-    // Newton loop decided on the device: when iter_ptr is set, the item list, its count, the
-    // next list and its count are the ping-pong pair selected by the iterate index *iter_ptr
-    const int* iter_ptr;
-    int* list_pp[2];
-    int* count_pp;
+    // cooperative Newton loop (newton_coop_kernel): passes run are added to *passes; the grid
+    // barrier counts on *coop_bar and flags a timed-out wait in *coop_err
+    int* passes;
+    unsigned* coop_bar;
+    int* coop_err;
+    unsigned long long coop_limit_ns;
     double f_tol, x_tol, fp_eps;
     int max_iter, fixed_point;
     double* label_y;             // MODE_LABEL: Phi - C
@@ -71,22 +76,24 @@ struct PathArgs {
 };
 
 // ---------------------------------------------------------------------------------------------
-// FP64 payoff at a start point (the item's own point; used by the Newton and label epilogues).
+// FP64 payoff at a start point (the item's own point in device memory; used by the Newton and
+// label epilogues).  The point is read through L2: in the cooperative Newton loop another SM may
+// have moved it in an earlier pass of the same launch.
 
 __device__ inline double payoff64(const PathArgs& a, const double* S, int d) {
     if (a.payoff == BAP_MAX_CALL) {
-        double mx = S[0];
-        for (int q = 1; q < d; ++q) mx = S[q] > mx ? S[q] : mx;
+        double mx = __ldcg(S);
+        for (int q = 1; q < d; ++q) mx = fmax(mx, __ldcg(S + q));
         double v = mx - a.K;
         return v > 0 ? v : 0;
     } else if (a.payoff == BAP_BASKET_PUT) {
         double b = 0;
-        for (int q = 0; q < d; ++q) b += a.model->w[q] * S[q];
+        for (int q = 0; q < d; ++q) b += a.model->w[q] * __ldcg(S + q);
         double v = a.K - b;
         return v > 0 ? v : 0;
     }
     double lg = 0;
-    for (int q = 0; q < d; ++q) lg += a.model->w[q] * log(S[q]);
+    for (int q = 0; q < d; ++q) lg += a.model->w[q] * log(__ldcg(S + q));
     double v = exp(lg) - a.K;
     return v > 0 ? v : 0;
 }
@@ -97,12 +104,29 @@ __device__ inline double payoff_dlog64(const PathArgs& a, const double* S, int d
     if (phi <= 0) return 0;
     if (a.payoff == BAP_MAX_CALL) {
         int best = 0;
-        for (int q = 1; q < d; ++q)
-            if (S[q] > S[best]) best = q;
-        return best == p ? S[p] : 0.0;
+        double sb = __ldcg(S);
+        for (int q = 1; q < d; ++q) {
+            const double sq = __ldcg(S + q);
+            if (sq > sb) { sb = sq; best = q; }
+        }
+        return best == p ? sb : 0.0;
     }
-    if (a.payoff == BAP_BASKET_PUT) return -a.model->w[p] * S[p];
+    if (a.payoff == BAP_BASKET_PUT) return -a.model->w[p] * __ldcg(S + p);
     return a.model->w[p] * (phi + a.K);
+}
+
+__device__ inline ItemState load_state_l2(const ItemState* p) {
+    ItemState s;
+    s.x = __ldcg(&p->x);
+    s.lo = __ldcg(&p->lo);
+    s.hi = __ldcg(&p->hi);
+    s.dx_old = __ldcg(&p->dx_old);
+    s.dx = __ldcg(&p->dx);
+    s.iters = __ldcg(&p->iters);
+    s.status = __ldcg(&p->status);
+    s.done = __ldcg(&p->done);
+    s.pivot = __ldcg(&p->pivot);
+    return s;
 }
 
 // Newton update of one boundary point after an evaluation of C(x) and C'(x) (FP64; the same
@@ -111,7 +135,9 @@ __device__ inline double payoff_dlog64(const PathArgs& a, const double* S, int d
 // doubling while no upper end is known).  Returns true if the item needs another evaluation.
 __device__ inline bool newton_update(const PathArgs& a, int item, double C, double dC) {
     const int d = a.model->d;
-    ItemState& s = a.state[item];
+    // The item's state and point may have been written on another SM in an earlier pass of
+    // the same launch (cooperative form): read them through L2, not a possibly stale L1 line.
+    ItemState s = load_state_l2(a.state + item);
     double* S = a.start + (size_t)item * d;
     const int p = s.pivot;
     const double K = a.K;
@@ -128,12 +154,12 @@ __device__ inline bool newton_update(const PathArgs& a, int item, double C, doub
         } else if (a.payoff == BAP_GEO_CALL) {
             double lg = log(K + C);
             for (int q = 0; q < d; ++q)
-                if (q != p) lg -= a.model->w[q] * log(S[q]);
+                if (q != p) lg -= a.model->w[q] * log(__ldcg(S + q));
             xn = exp(lg / a.model->w[p]);
         } else {
             double v = K - C;
             for (int q = 0; q < d; ++q)
-                if (q != p) v -= a.model->w[q] * S[q];
+                if (q != p) v -= a.model->w[q] * __ldcg(S + q);
             xn = v / a.model->w[p];
             if (xn < 0) xn = 0;
         }
@@ -179,6 +205,7 @@ __device__ inline bool newton_update(const PathArgs& a, int item, double C, doub
     s.x = x;
     S[p] = x;
     s.done = done ? 1 : 0;
+    a.state[item] = s;
     return !done;
 }
 
@@ -219,7 +246,56 @@ __device__ __forceinline__ void load_vec(const double* src, double (&dst)[N]) {
     }
 }
 
-template <int D, int RULE, typename Real>
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned load_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.  *bar counts block arrivals
+// over the whole launch (zero before it); barrier number g = 1, 2, ... is passed once it reaches
+// g * gridDim.x.  A block that waits longer than limit_ns, or sees *err set by another block,
+// sets *err and gets false: the caller then leaves the kernel, so every block ends in bounded
+// time and the host reads the flag.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned g, int* err, unsigned long long limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = g * gridDim.x;
+        const unsigned long long t0 = global_ns();
+        while (load_acquire_gpu(bar) < target) {
+            if (*(volatile int*)err != 0 || global_ns() - t0 > limit_ns) {
+                atomicExch(err, 1);
+                good = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The path kernel.  Plain form (COOP = false): one pass, `it` = pass_it or *iter_ptr.
+// Cooperative form (COOP = true, I&Z Newton only): every Newton pass of one date in one launch,
+// it = 0, 1, ..., on the same lists, counts and unit counters as the plain form (all zero
+// before the launch); a grid barrier ends each pass, after which all blocks read the same next
+// count, so all run the same passes.  Its grid must be co-resident (cudaLaunchCooperativeKernel
+// checks that); the barrier's wait is bounded all the same (coop_err, coop_limit_ns).
+// The unit loop is written once, in this kernel body: moved into an inlined device function it
+// compiled measurably slower.
+template <int D, int RULE, typename Real, bool COOP>
 __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NF = D + 1;
@@ -254,299 +330,301 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const int* active = a.active;
-    const int* n_active = a.n_active;
-    int* next_active = a.next_active;
-    int* next_count = a.next_count;
-    if (a.iter_ptr) {
-        const int itv = *a.iter_ptr;
-        active = a.list_pp[itv & 1];
-        n_active = a.count_pp + (itv & 1);
-        next_active = a.list_pp[(itv + 1) & 1];
-        next_count = a.count_pp + ((itv + 1) & 1);
-    }
-    const long long total_units = (long long)(*n_active) * a.C;
     const Real K = (Real)a.K;
     const bool is_put = a.payoff == BAP_BASKET_PUT;
     const bool is_max = a.payoff == BAP_MAX_CALL;
 
     // The Cholesky factor and the per-step drift are read straight from the kernel parameters
     // (constant bank operands, no registers).
+    // (The FP64 check kernels read them from the device model instead.)
     auto Lc = [&](int q, int j) -> Real {
-        if constexpr (sizeof(Real) == 4) return a.Lf[q * MAXD + j];
-        else return a.Ld[q * MAXD + j];
+        if constexpr (sizeof(Real) == 4) return a.Lf[q * (q + 1) / 2 + j];
+        else return M->L[q * MAXD + j] * (a.uniform ? M->vol2[1][q] : 1.0);
     };
     auto drift_c = [&](int q) -> Real {
         if constexpr (sizeof(Real) == 4) return a.driftf[q];
-        else return a.driftd[q];
+        else return M->drift2[1][q];
     };
 
-    while (true) {
-        unsigned long long unit_u = 0;
-        if (lane == 0) unit_u = atomicAdd(a.work, 1ULL);
-        const long long unit = (long long)__shfl_sync(FULL, unit_u, 0);
-        if (unit >= total_units) break;
-        const int slot = (int)(unit / a.C);
-        const int chunk = (int)(unit - (long long)slot * a.C);
-        const int item = active ? active[slot] : slot;
 
-        // log2 of the start point in FP64, one coordinate per lane, then broadcast
-        const double* st = a.start + (size_t)item * D;
-        const double my_l0 = lane < D ? log2(st[lane]) : 0.0;
-        Real l0[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
-        const int pivot = a.pivot ? a.pivot[item] : -1;
-        // The unit covers paths n_begin .. n_begin + n_count - 1.  Inside the loop only the
-        // 32-bit offset nl moves: counter word 0 is (n_begin + nl) mod 2^32 and word 1 stays
-        // item + n_begin / 2^32 (a unit never straddles a multiple of 2^32 paths).
-        const long long n_begin = (long long)chunk * a.chunk;
-        const int n_count = (int)min((long long)a.chunk, (long long)a.N - n_begin);
-        const uint32_t w0_base = (uint32_t)n_begin;
-        const uint32_t w1_word = (a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u) + (uint32_t)(n_begin >> 32);
+    int it = COOP ? 0 : (a.iter_ptr ? *a.iter_ptr : a.pass_it);
+    bool ok = true;
+    for (;;) {
+    // ---- one pass: every unit of the count[it] items of list[it & 1] ----
+    const long long total_units = (long long)__ldcg(a.count + it) * a.C;
+        while (true) {
+            unsigned long long unit_u = 0;
+            if (lane == 0) unit_u = atomicAdd(a.work + it, 1ULL);
+            const long long unit = (long long)__shfl_sync(FULL, unit_u, 0);
+            if (unit >= total_units) break;
+            const int slot = (int)(unit / a.C);
+            const int chunk = (int)(unit - (long long)slot * a.C);
+            const int* active = a.list[it & 1];
+            const int item = active ? __ldcg(active + slot) : slot;
 
-        int nl = lane;
-        bool has = nl < n_count;
-        int next = 32;
-        Real l[D];
+            // log2 of the start point in FP64, one coordinate per lane, then broadcast
+            const double* st = a.start + (size_t)item * D;
+            const double my_l0 = lane < D ? log2(__ldcg(st + lane)) : 0.0;
+            Real l0[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) l[q] = l0[q];
-        int k = a.m;
-        Real acc0 = 0, acc1 = 0, acc2 = 0;
-        double s0 = 0, s1 = 0, s2 = 0;
-        int steps = 0;
+            for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
+            const int pivot = a.pivot ? a.pivot[item] : -1;
+            // The unit covers paths n_begin .. n_begin + n_count - 1.  Inside the loop only the
+            // 32-bit offset nl moves: counter word 0 is (n_begin + nl) mod 2^32 and word 1 stays
+            // item + n_begin / 2^32 (a unit never straddles a multiple of 2^32 paths).
+            const long long n_begin = (long long)chunk * a.chunk;
+            const int n_count = (int)min((long long)a.chunk, (long long)a.N - n_begin);
+            const uint32_t w0_base = (uint32_t)n_begin;
+            const uint32_t w1_word = (a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u) + (uint32_t)(n_begin >> 32);
 
-        // Blocks of up to 32 warp steps; the FP32 partial sums move to FP64 after each block
-        // (a lane ends at most 32 paths in between).  The flush sits outside the inner loop on
-        // purpose: inside it the compiler would evaluate it speculatively on every step, and the
-        // FP64 pipe runs at 1/64 of the FP32 rate.
-        bool live = true;
-        while (live) {
-        for (int it = 0; it < 32; ++it) {
-            live = __any_sync(FULL, has);
-            if (!live) break;
-            bool finished = false;
-            if (has) {
-                k += 1;
-                ++steps;
-                Real z[D];
-                normals<D, Real>(w0_base + (uint32_t)nl, w1_word, (uint32_t)k, a.rk, z);
-                if (a.uniform) {
+            int nl = lane;
+            bool has = nl < n_count;
+            int next = 32;
+            Real l[D];
 #pragma unroll
-                    for (int q = 0; q < D; ++q) {
-                        Real wq = 0;
+            for (int q = 0; q < D; ++q) l[q] = l0[q];
+            int k = a.m;
+            Real acc0 = 0, acc1 = 0, acc2 = 0;
+            double s0 = 0, s1 = 0, s2 = 0;
+            int steps = 0;
+
+            // Blocks of up to 32 warp steps; the FP32 partial sums move to FP64 after each block
+            // (a lane ends at most 32 paths in between).  The flush sits outside the inner loop on
+            // purpose: inside it the compiler would evaluate it speculatively on every step, and the
+            // FP64 pipe runs at 1/64 of the FP32 rate.
+            bool live = true;
+            while (live) {
+            for (int it = 0; it < 32; ++it) {
+                live = __any_sync(FULL, has);
+                if (!live) break;
+                bool finished = false;
+                if (has) {
+                    k += 1;
+                    ++steps;
+                    Real z[D];
+                    normals<D, Real>(w0_base + (uint32_t)nl, w1_word, (uint32_t)k, a.rk, z);
+                    if (a.uniform) {
 #pragma unroll
-                        for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
-                        l[q] = l[q] + drift_c(q) + wq;
-                    }
-                } else {
-                    const int kk = (k - a.m - 1) * D;
+                        for (int q = 0; q < D; ++q) {
+                            Real wq = 0;
 #pragma unroll
-                    for (int q = 0; q < D; ++q) {
-                        Real wq = 0;
-#pragma unroll
-                        for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
-                        l[q] = fma(sh_vol[kk + q], wq, l[q] + sh_drift[kk + q]);
-                    }
-                }
-                // prices and payoff
-                Real S[D];
-#pragma unroll
-                for (int q = 0; q < D; ++q) S[q] = PathMath<Real>::exp2r(l[q]);
-                int imax = 0;
-                Real lmax = l[0];
-#pragma unroll
-                for (int q = 1; q < D; ++q)
-                    if (l[q] > lmax) { lmax = l[q]; imax = q; }
-                Real phi;
-                Real gval = 0;
-                if (is_max) {
-                    Real smax = S[0];
-#pragma unroll
-                    for (int q = 1; q < D; ++q) smax = (q == imax) ? S[q] : smax;
-                    phi = smax - K;
-                } else if (is_put) {
-                    Real b = 0;
-#pragma unroll
-                    for (int q = 0; q < D; ++q) b = fma((Real)a.wf[q], S[q], b);
-                    phi = K - b;
-                } else {
-                    Real lg = 0;
-#pragma unroll
-                    for (int q = 0; q < D; ++q) lg = fma((Real)a.wf[q], l[q], lg);
-                    gval = PathMath<Real>::exp2r(lg);
-                    phi = gval - K;
-                }
-                bool ex = phi > 0;
-                if (ex && k < a.n_dates) {
-                    const int kr = k - a.m - 1;
-                    if (RULE == R_NONE || !sh_fit[kr]) {
-                        ex = false;
-                    } else if (RULE == R_IZ) {
-                        // exercise iff S_p passes B''(S_{-p}) (full quadratic, Horner order)
-                        const int p = is_max ? imax : 0;
-                        Real sp = S[0];
-#pragma unroll
-                        for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
-                        Real cc[P4];
-                        load_vec<P4>(sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
-                        Real B = cc[0];
-                        if constexpr (D > 1) {
-                            Real y[D - 1];
-#pragma unroll
-                            for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
-                            int idx = 1;
-#pragma unroll
-                            for (int t = 0; t < D - 1; ++t) {
-                                Real acc = cc[idx++];
-#pragma unroll
-                                for (int u = t; u < D - 1; ++u) acc = fma(cc[idx++], y[u], acc);
-                                B = fma(acc, y[t], B);
-                            }
+                            for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
+                            l[q] = l[q] + drift_c(q) + wq;
                         }
-                        ex = is_put ? (sp <= B) : (sp >= B);
-                    } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
-                        const Real* rec = sh_rule + kr * a.rule_stride;
-                        Real F = rec[0];
+                    } else {
+                        const int kk = (k - a.m - 1) * D;
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) {
-                            int nf, off;
-                            if constexpr (sizeof(Real) == 4) {
-                                nf = __float_as_int((float)rec[2 + f]);
-                                off = __float_as_int((float)rec[2 + NF + f]);
-                            } else {
-                                nf = (int)__double_as_longlong((double)rec[2 + f]);
-                                off = (int)__double_as_longlong((double)rec[2 + NF + f]);
-                            }
-                            if (nf > 0) {
-                                Real xv = phi;
+                        for (int q = 0; q < D; ++q) {
+                            Real wq = 0;
 #pragma unroll
-                                for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
-                                int lo = 0, hi = nf;
-                                while (lo < hi) {
-                                    const int mid = (lo + hi) >> 1;
-                                    if (rec[off + mid] < xv) lo = mid + 1; else hi = mid;
+                            for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
+                            l[q] = fma(sh_vol[kk + q], wq, l[q] + sh_drift[kk + q]);
+                        }
+                    }
+                    // prices and payoff
+                    Real S[D];
+#pragma unroll
+                    for (int q = 0; q < D; ++q) S[q] = PathMath<Real>::exp2r(l[q]);
+                    int imax = 0;
+                    Real lmax = l[0];
+#pragma unroll
+                    for (int q = 1; q < D; ++q)
+                        if (l[q] > lmax) { lmax = l[q]; imax = q; }
+                    Real phi;
+                    Real gval = 0;
+                    if (is_max) {
+                        Real smax = S[0];
+#pragma unroll
+                        for (int q = 1; q < D; ++q) smax = (q == imax) ? S[q] : smax;
+                        phi = smax - K;
+                    } else if (is_put) {
+                        Real b = 0;
+#pragma unroll
+                        for (int q = 0; q < D; ++q) b = fma((Real)a.wf[q], S[q], b);
+                        phi = K - b;
+                    } else {
+                        Real lg = 0;
+#pragma unroll
+                        for (int q = 0; q < D; ++q) lg = fma((Real)a.wf[q], l[q], lg);
+                        gval = PathMath<Real>::exp2r(lg);
+                        phi = gval - K;
+                    }
+                    bool ex = phi > 0;
+                    if (ex && k < a.n_dates) {
+                        const int kr = k - a.m - 1;
+                        if (RULE == R_NONE || !sh_fit[kr]) {
+                            ex = false;
+                        } else if (RULE == R_IZ) {
+                            // exercise iff S_p passes B''(S_{-p}) (full quadratic, Horner order)
+                            const int p = is_max ? imax : 0;
+                            Real sp = S[0];
+#pragma unroll
+                            for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
+                            Real cc[P4];
+                            load_vec<P4>(sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
+                            Real B = cc[0];
+                            if constexpr (D > 1) {
+                                Real y[D - 1];
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
+                                int idx = 1;
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) {
+                                    Real acc = cc[idx++];
+#pragma unroll
+                                    for (int u = t; u < D - 1; ++u) acc = fma(cc[idx++], y[u], acc);
+                                    B = fma(acc, y[t], B);
                                 }
-                                F += rec[off + nf + lo];
+                            }
+                            ex = is_put ? (sp <= B) : (sp >= B);
+                        } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
+                            const Real* rec = sh_rule + kr * a.rule_stride;
+                            Real F = rec[0];
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) {
+                                int nf, off;
+                                if constexpr (sizeof(Real) == 4) {
+                                    nf = __float_as_int((float)rec[2 + f]);
+                                    off = __float_as_int((float)rec[2 + NF + f]);
+                                } else {
+                                    nf = (int)__double_as_longlong((double)rec[2 + f]);
+                                    off = (int)__double_as_longlong((double)rec[2 + NF + f]);
+                                }
+                                if (nf > 0) {
+                                    Real xv = phi;
+#pragma unroll
+                                    for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
+                                    int lo = 0, hi = nf;
+                                    while (lo < hi) {
+                                        const int mid = (lo + hi) >> 1;
+                                        if (rec[off + mid] < xv) lo = mid + 1; else hi = mid;
+                                    }
+                                    F += rec[off + nf + lo];
+                                }
+                            }
+                            ex = F > 0;
+                        }
+                    }
+                    if (ex || k == a.n_dates) {
+                        finished = true;
+                        Real v = 0, dv = 0;
+                        if (ex) {
+                            const Real disc = sh_disc[k - a.m - 1];
+                            v = disc * phi;
+                            if (pivot >= 0) {
+                                if (is_max) {
+                                    dv = (imax == pivot) ? disc * (phi + K) : (Real)0;
+                                } else if (is_put) {
+                                    Real sp = S[0], wp = (Real)a.wf[0];
+#pragma unroll
+                                    for (int q = 1; q < D; ++q) {
+                                        sp = (q == pivot) ? S[q] : sp;
+                                        wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                                    }
+                                    dv = -disc * wp * sp;
+                                } else {
+                                    Real wp = (Real)a.wf[0];
+#pragma unroll
+                                    for (int q = 1; q < D; ++q) wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                                    dv = disc * wp * gval;
+                                }
                             }
                         }
-                        ex = F > 0;
+                        if (a.mode == MODE_TRACE) {
+                            a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
+                            a.trace_phi[n_begin + nl] = (double)v;
+                        }
+                        acc0 += v;
+                        acc1 += v * v;
+                        acc2 += dv;
                     }
                 }
-                if (ex || k == a.n_dates) {
-                    finished = true;
-                    Real v = 0, dv = 0;
-                    if (ex) {
-                        const Real disc = sh_disc[k - a.m - 1];
-                        v = disc * phi;
-                        if (pivot >= 0) {
-                            if (is_max) {
-                                dv = (imax == pivot) ? disc * (phi + K) : (Real)0;
-                            } else if (is_put) {
-                                Real sp = S[0], wp = (Real)a.wf[0];
+                const unsigned need = __ballot_sync(FULL, finished);
+                if (need) {
+                    if (finished) {
+                        nl = next + __popc(need & lanemask_lt);
+                        has = nl < n_count;
 #pragma unroll
-                                for (int q = 1; q < D; ++q) {
-                                    sp = (q == pivot) ? S[q] : sp;
-                                    wp = (q == pivot) ? (Real)a.wf[q] : wp;
-                                }
-                                dv = -disc * wp * sp;
-                            } else {
-                                Real wp = (Real)a.wf[0];
-#pragma unroll
-                                for (int q = 1; q < D; ++q) wp = (q == pivot) ? (Real)a.wf[q] : wp;
-                                dv = disc * wp * gval;
-                            }
-                        }
+                        for (int q = 0; q < D; ++q) l[q] = l0[q];
+                        k = a.m;
                     }
-                    if (a.mode == MODE_TRACE) {
-                        a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
-                        a.trace_phi[n_begin + nl] = (double)v;
-                    }
-                    acc0 += v;
-                    acc1 += v * v;
-                    acc2 += dv;
+                    next += __popc(need);
                 }
             }
-            const unsigned need = __ballot_sync(FULL, finished);
-            if (need) {
-                if (finished) {
-                    nl = next + __popc(need & lanemask_lt);
-                    has = nl < n_count;
-#pragma unroll
-                    for (int q = 0; q < D; ++q) l[q] = l0[q];
-                    k = a.m;
-                }
-                next += __popc(need);
+            s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
+            acc0 = acc1 = acc2 = 0;
             }
-        }
-        s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
-        acc0 = acc1 = acc2 = 0;
-        }
-        long long steps64 = steps;
+            long long steps64 = steps;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            s0 += __shfl_down_sync(FULL, s0, off);
-            s1 += __shfl_down_sync(FULL, s1, off);
-            s2 += __shfl_down_sync(FULL, s2, off);
-            steps64 += __shfl_down_sync(FULL, steps64, off);
-        }
-        int last = 0;
-        if (lane == 0) {
-            const size_t o = (size_t)item * a.C + chunk;
-            a.partial[3 * o + 0] = s0;
-            a.partial[3 * o + 1] = s1;
-            a.partial[3 * o + 2] = s2;
-            a.partial_steps[o] = steps64;
+            for (int off = 16; off > 0; off >>= 1) {
+                s0 += __shfl_down_sync(FULL, s0, off);
+                s1 += __shfl_down_sync(FULL, s1, off);
+                s2 += __shfl_down_sync(FULL, s2, off);
+                steps64 += __shfl_down_sync(FULL, steps64, off);
+            }
+            int last = 0;
+            if (lane == 0) {
+                const size_t o = (size_t)item * a.C + chunk;
+                a.partial[3 * o + 0] = s0;
+                a.partial[3 * o + 1] = s1;
+                a.partial[3 * o + 2] = s2;
+                a.partial_steps[o] = steps64;
+                __threadfence();
+                last = atomicAdd(&a.done[item], 1) == a.C - 1;
+            }
+            last = __shfl_sync(FULL, last, 0);
+            if (!last) continue;
+
+            // ---- the warp that finished the item's last unit: fixed-order sum over its units ----
             __threadfence();
-            last = atomicAdd(&a.done[item], 1) == a.C - 1;
-        }
-        last = __shfl_sync(FULL, last, 0);
-        if (!last) continue;
-
-        // ---- the warp that finished the item's last unit: fixed-order sum over its units ----
-        __threadfence();
-        double t0 = 0, t1 = 0, t2 = 0;
-        long long ts = 0;
-        for (int c = lane; c < a.C; c += 32) {
-            const size_t o = (size_t)item * a.C + c;
-            t0 += __ldcg(a.partial + 3 * o + 0);
-            t1 += __ldcg(a.partial + 3 * o + 1);
-            t2 += __ldcg(a.partial + 3 * o + 2);
-            ts += __ldcg(a.partial_steps + o);
-        }
+            double t0 = 0, t1 = 0, t2 = 0;
+            long long ts = 0;
+            for (int c = lane; c < a.C; c += 32) {
+                const size_t o = (size_t)item * a.C + c;
+                t0 += __ldcg(a.partial + 3 * o + 0);
+                t1 += __ldcg(a.partial + 3 * o + 1);
+                t2 += __ldcg(a.partial + 3 * o + 2);
+                ts += __ldcg(a.partial_steps + o);
+            }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            t0 += __shfl_down_sync(FULL, t0, off);
-            t1 += __shfl_down_sync(FULL, t1, off);
-            t2 += __shfl_down_sync(FULL, t2, off);
-            ts += __shfl_down_sync(FULL, ts, off);
-        }
-        if (lane == 0) {
-            a.done[item] = 0;
-            atomicAdd(a.total_steps, (unsigned long long)ts);
-            const double Nd = (double)a.N;
-            if (a.mode == MODE_SUMS || a.mode == MODE_TRACE) {
-                // the pathwise derivative is with respect to the pivot's start value x
-                const int pv = a.pivot ? a.pivot[item] : -1;
-                const double xs = pv >= 0 ? a.start[(size_t)item * D + pv] : 1.0;
-                a.out_sums[3 * item + 0] = t0;
-                a.out_sums[3 * item + 1] = t1;
-                a.out_sums[3 * item + 2] = t2 / xs;
-                a.out_steps[item] = ts;
-            } else if (a.mode == MODE_NEWTON) {
-                const double x = a.state[item].x;
-                if (newton_update(a, item, t0 / Nd, t2 / (Nd * x))) {
-                    const int pos = atomicAdd(next_count, 1);
-                    next_active[pos] = item;
+            for (int off = 16; off > 0; off >>= 1) {
+                t0 += __shfl_down_sync(FULL, t0, off);
+                t1 += __shfl_down_sync(FULL, t1, off);
+                t2 += __shfl_down_sync(FULL, t2, off);
+                ts += __shfl_down_sync(FULL, ts, off);
+            }
+            if (lane == 0) {
+                a.done[item] = 0;
+                atomicAdd(a.total_steps, (unsigned long long)ts);
+                const double Nd = (double)a.N;
+                if (a.mode == MODE_SUMS || a.mode == MODE_TRACE) {
+                    // the pathwise derivative is with respect to the pivot's start value x
+                    const int pv = a.pivot ? a.pivot[item] : -1;
+                    const double xs = pv >= 0 ? a.start[(size_t)item * D + pv] : 1.0;
+                    a.out_sums[3 * item + 0] = t0;
+                    a.out_sums[3 * item + 1] = t1;
+                    a.out_sums[3 * item + 2] = t2 / xs;
+                    a.out_steps[item] = ts;
+                } else if (a.mode == MODE_NEWTON) {
+                    const double x = __ldcg(&a.state[item].x);
+                    if (newton_update(a, item, t0 / Nd, t2 / (Nd * x))) {
+                        const int pos = atomicAdd(a.count + it + 1, 1);
+                        a.list[(it + 1) & 1][pos] = item;
+                    }
+                } else if (a.mode == MODE_LABEL) {
+                    const double phi = payoff64(a, a.start + (size_t)item * D, D);
+                    const double y = phi - t0 / Nd;
+                    a.label_y[item] = y;
+                    a.label[item] = y > 0 ? 1 : -1;
                 }
-            } else if (a.mode == MODE_LABEL) {
-                const double phi = payoff64(a, a.start + (size_t)item * D, D);
-                const double y = phi - t0 / Nd;
-                a.label_y[item] = y;
-                a.label[item] = y > 0 ? 1 : -1;
             }
         }
+    if constexpr (!COOP) break;
+    ok = grid_barrier(a.coop_bar, (unsigned)(it + 1), a.coop_err, a.coop_limit_ns);
+    if (!ok || __ldcg(a.count + it + 1) == 0 || it + 1 >= a.max_iter) break;
+    ++it;
     }
+    if (COOP && ok && blockIdx.x == 0 && threadIdx.x == 0 && a.passes) *a.passes += it + 1;
 }
 
 }  // namespace bap

@@ -30,8 +30,7 @@ enum ReqState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2 };
 
 struct Request {
     uint64_t ticket = 0;
-    std::vector<double> S0, sigma, delta, rho, dates, weights;
-    bap_model md{};
+    DevModel hm{};                 // validated and prepared at submit
     int method = 0;
     bap_iz_params iz{};
     bap_cmc_params cmc{};
@@ -54,11 +53,12 @@ struct bap_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
     std::vector<Request*> running;                 // touched by the server thread only
+    std::vector<bap_option*> free_slots;           // idle options kept for reuse (server thread)
     std::unordered_map<uint64_t, Request*> table;  // all requests not yet collected
     size_t budget = 0, used = 0;
     int max_inflight = 0;
     int device = 0;
-    int launch_mode = LAUNCH_GRAPH;
+    int launch_mode = LAUNCH_COOP;
     bool stop = false;
     uint64_t next_ticket = 1;
     bap_server_stats stats{};
@@ -67,31 +67,33 @@ struct bap_server {
 
 namespace {
 
-void copy_model(Request* r, const bap_model* md) {
-    const int d = md->d;
-    r->S0.assign(md->S0, md->S0 + d);
-    r->sigma.assign(md->sigma, md->sigma + d);
-    r->delta.assign(md->delta, md->delta + d);
-    r->rho.assign(md->rho, md->rho + (size_t)d * d);
-    if (md->dates) r->dates.assign(md->dates, md->dates + md->n_dates);
-    if (md->weights) r->weights.assign(md->weights, md->weights + d);
-    r->md = *md;
-    r->md.S0 = r->S0.data();
-    r->md.sigma = r->sigma.data();
-    r->md.delta = r->delta.data();
-    r->md.rho = r->rho.data();
-    r->md.dates = md->dates ? r->dates.data() : nullptr;
-    r->md.weights = md->weights ? r->weights.data() : nullptr;
-}
-
 // Starts a request on its own stream; false if it failed before anything was enqueued.
+// Starts a request on an idle option slot (a new one if none is idle); false if it failed
+// before anything was enqueued.
 bool start_request(bap_server* s, Request* r) {
     clear_error();
-    bap_status st = option_create(&r->md, &r->opt);
-    if (st == BAP_OK) r->opt->launch_mode = s->launch_mode;
+    bap_status st = BAP_OK;
+    if (!s->free_slots.empty()) {
+        r->opt = s->free_slots.back();
+        s->free_slots.pop_back();
+    } else {
+        st = option_alloc(&r->opt);
+    }
+    const auto t0 = Clock::now();
+    if (st == BAP_OK) st = option_load(r->opt, r->hm);
+    const auto t1 = Clock::now();
+    if (st == BAP_OK) {
+        r->opt->launch_mode = s->launch_mode;
+        r->opt->grid_share = std::min(s->max_inflight, 8);
+    }
     if (st == BAP_OK)
         st = r->method == BAP_METHOD_IZ ? enqueue_fit_iz(r->opt, &r->iz) : enqueue_fit_cmc(r->opt, &r->cmc);
+    const auto t2 = Clock::now();
     if (st == BAP_OK) st = enqueue_price(r->opt, r->n_paths, r->seed);
+    const auto t3 = Clock::now();
+    s->stats.load_ms += ms_between(t0, t1);
+    s->stats.fit_enqueue_ms += ms_between(t1, t2);
+    s->stats.price_enqueue_ms += ms_between(t2, t3);
     if (st == BAP_OK && cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess)
         st = fail(BAP_ECUDA, "event create");
     if (st == BAP_OK && cudaEventRecord(r->done_ev, r->opt->stream) != cudaSuccess)
@@ -113,10 +115,14 @@ void finish_request(Request* r) {
     if (st != BAP_OK && st != BAP_ENOCONV) r->err = error_text();
 }
 
-void release(Request* r) {
+// Returns the request's option to the idle slots (destroys it after a device error).
+void release(bap_server* s, Request* r) {
     if (r->done_ev) cudaEventDestroy(r->done_ev);
     r->done_ev = nullptr;
-    if (r->opt) option_destroy(r->opt);
+    if (r->opt) {
+        if (r->status == BAP_ECUDA) option_destroy(r->opt);
+        else s->free_slots.push_back(r->opt);
+    }
     r->opt = nullptr;
 }
 
@@ -140,10 +146,13 @@ void server_loop(bap_server* s) {
             s->stats.peak_bytes = std::max<int64_t>(s->stats.peak_bytes, (int64_t)s->used);
         }
         for (Request* r : admit) {
-            if (start_request(s, r)) {
+            const auto t0 = Clock::now();
+            const bool ok = start_request(s, r);
+            s->stats.start_ms += ms_between(t0, Clock::now());
+            if (ok) {
                 s->running.push_back(r);
             } else {
-                release(r);
+                release(s, r);
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->used -= r->mem;
                 r->state = Q_DONE;
@@ -164,13 +173,15 @@ void server_loop(bap_server* s) {
                 ++i;
                 continue;
             }
+            const auto t0 = Clock::now();
             if (q == cudaSuccess) {
                 finish_request(r);
             } else {
                 r->status = BAP_ECUDA;
                 r->err = cudaGetErrorString(q);
             }
-            release(r);
+            release(s, r);
+            s->stats.finish_ms += ms_between(t0, Clock::now());
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->used -= r->mem;
@@ -190,6 +201,8 @@ void server_loop(bap_server* s) {
                 s->cv_work.wait_for(lk, std::chrono::microseconds(s->running.empty() ? 2000 : 50));
         }
     }
+    for (bap_option* o : s->free_slots) option_destroy(o);
+    s->free_slots.clear();
 }
 
 }  // namespace
@@ -222,7 +235,8 @@ bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_ser
 
 bap_status bap_server_set_launch_mode(bap_server* s, int mode) {
     if (!s) return fail(BAP_EINVAL, "null server");
-    if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH) return fail(BAP_EINVAL, "bad launch mode");
+    if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH && mode != LAUNCH_COOP)
+        return fail(BAP_EINVAL, "bad launch mode");
     std::lock_guard<std::mutex> lk(s->mu);
     s->launch_mode = mode;
     return BAP_OK;
@@ -239,7 +253,11 @@ bap_status bap_submit(bap_server* s, const bap_model* md, int method, const void
     if (n_paths < 2 || n_paths > (1LL << 40)) return fail(BAP_EINVAL, "n_paths outside 2..2^40");
     Request* r = new (std::nothrow) Request();
     if (!r) return fail(BAP_ENOMEM, "host allocation");
-    copy_model(r, md);
+    const bap_status sm = model_prepare(md, &r->hm);
+    if (sm != BAP_OK) {
+        delete r;
+        return sm;
+    }
     r->method = method;
     bap_status st = BAP_OK;
     if (method == BAP_METHOD_IZ) {
@@ -255,7 +273,7 @@ bap_status bap_submit(bap_server* s, const bap_model* md, int method, const void
     }
     r->n_paths = n_paths;
     r->seed = seed;
-    r->mem = estimate_bytes(&r->md, method, params, n_paths);
+    r->mem = estimate_bytes(md, method, params, n_paths);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
         delete r;

@@ -39,6 +39,18 @@ def test_graph_and_plain_launch_forms_agree():
     # the graph runs only the Newton passes that are needed
     assert rb["kernel_launches"] < ra["kernel_launches"]
     assert rb["path_launches"] < ra["path_launches"]
+    # one cooperative launch per date runs all of its passes
+    c = _fit(spec, params, bap.LAUNCH_COOP)
+    for m in range(1, spec.n_dates):
+        xa, ia, sa = a.fit_points(m)
+        xc, ic, sc = c.fit_points(m)
+        assert np.array_equal(xa, xc) and np.array_equal(ia, ic) and np.array_equal(sa, sc), m
+    rc = c.price(100_000, 5)
+    assert rc["price"] == ra["price"] and rc["var"] == ra["var"]
+    assert rc["fit_path_steps"] == ra["fit_path_steps"]
+    # fit: one cooperative launch per date; pricing: the same launches as the other forms
+    assert rc["path_launches"] - (spec.n_dates - 1) == ra["path_launches"] - (spec.n_dates - 1) * params.max_iter
+    c.close()
     # replay of the same graph, and a rebuild for new parameters
     b.fit_boundary(params)
     assert b.price(100_000, 5)["price"] == rb["price"]
