@@ -8,7 +8,8 @@
 // loop can keep many options in flight.
 #include <algorithm>
 #include <cmath>
-#include <unordered_map>
+#include <map>
+#include <vector>
 
 #include "bap_host.cuh"
 
@@ -80,14 +81,42 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Per (kernel, device): whether its dynamic shared-memory limit is raised, and the cached
+// occupancy for the last shared-memory size asked about.
 struct FnInfo {
-    int blocks_per_sm = 0;
-    size_t smem_set = 0;
-    size_t occ_smem = ~size_t(0);   // shared-memory size of the cached occupancy query
+    bool smem_raised = false;
+    size_t occ_smem = ~size_t(0);
     int occ_blocks = 0;
 };
 std::mutex g_fn_mu;
-std::unordered_map<const void*, FnInfo> g_fn;
+std::map<std::pair<const void*, int>, FnInfo> g_fn;
+
+// Raise a kernel's dynamic shared-memory limit to everything the device allows, once per device
+// (call with g_fn_mu held).  Changing the attribute waits for running launches of the kernel,
+// so it must not happen again once requests are in flight.
+bap_status raise_smem_limit(const void* fn, int device, FnInfo& fi) {
+    if (fi.smem_raised) return BAP_OK;
+    int optin = 0;
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    cudaFuncAttributes fa;
+    CU(cudaFuncGetAttributes(&fa, fn));
+    CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    fi.smem_raised = true;
+    return BAP_OK;
+}
+
+// Resident blocks per SM of a path kernel at this dynamic shared-memory size.
+bap_status path_blocks_per_sm(const void* fn, int device, size_t smem, int* bps) {
+    std::lock_guard<std::mutex> lk(g_fn_mu);
+    FnInfo& fi = g_fn[{fn, device}];
+    TRY(raise_smem_limit(fn, device, fi));
+    if (fi.occ_smem != smem) {
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fi.occ_blocks, fn, kBlock, smem));
+        fi.occ_smem = smem;
+    }
+    *bps = std::max(1, fi.occ_blocks);
+    return BAP_OK;
+}
 
 const void* path_fn(int D, int rule, bool fp64) {
     switch (D) {
@@ -136,21 +165,8 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
     const size_t smem = path_smem_bytes(a, rule, fp64, o->d);
     if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
-    int bps;
-    {
-        std::lock_guard<std::mutex> lk(g_fn_mu);
-        FnInfo& fi = g_fn[fn];
-        if (smem > fi.smem_set) {
-            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
-            fi.smem_set = std::max<size_t>(smem, 48 * 1024);
-        }
-        if (fi.occ_smem != smem) {
-            CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fi.occ_blocks, fn, kBlock, smem));
-            fi.occ_smem = smem;
-        }
-        bps = fi.occ_blocks;
-    }
-    if (bps < 1) bps = 1;
+    int bps = 1;
+    TRY(path_blocks_per_sm(fn, o->device, smem, &bps));
     long long blocks = (max_units + (kBlock / 32) - 1) / (kBlock / 32);
     long long cap = (long long)o->sm_count * bps;
     const bool coop = rule == R_NEWTON_COOP;
@@ -642,11 +658,50 @@ bap_status model_prepare(const bap_model* md, DevModel* out) {
     return BAP_OK;
 }
 
+// CUDA loads a kernel on its first use, and that load waits for the work already running on
+// the device: under concurrent requests a first use stalled the calling thread for up to a
+// second.  So all kernels of the library are loaded (and the shared-memory limits of those that
+// need more than the default raised) once per device, when the first option or server is made.
+bap_status preload_kernels(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return BAP_OK;
+    {
+        std::lock_guard<std::mutex> lk2(g_fn_mu);
+        for (int D = 1; D <= MAXD; ++D) {
+            for (int rule : {(int)R_NONE, (int)R_IZ, (int)R_CMC, R_NEWTON_COOP}) {
+                for (int fp64 = 0; fp64 < (rule == R_NEWTON_COOP ? 1 : 2); ++fp64) {
+                    const void* fn = path_fn(D, rule, fp64 != 0);
+                    TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+                }
+            }
+        }
+        const void* ab = (const void*)adaboost_kernel;
+        TRY(raise_smem_limit(ab, device, g_fn[{ab, device}]));
+    }
+    const void* others[] = {
+        (const void*)iota_kernel,          (const void*)korobov_merit_kernel,
+        (const void*)korobov_pick_kernel,  (const void*)iz_setup_kernel,
+        (const void*)stage_iz_kernel,      (const void*)ls_fit_kernel,
+        (const void*)train_points_kernel,  (const void*)stage_cmc_kernel,
+        (const void*)newton_decide_kernel, (const void*)set_int_kernel,
+        (const void*)rng_debug_kernel,     (const void*)collect_points_kernel,
+        (const void*)collect_labels_kernel};
+    for (const void* fn : others) {
+        cudaFuncAttributes fa;
+        CU(cudaFuncGetAttributes(&fa, fn));
+    }
+    done.push_back(device);
+    return BAP_OK;
+}
+
 // Stream, events and page-locked results of an option, without a model yet.
 bap_status option_alloc(bap_option** out) {
     *out = nullptr;
     int dev;
     if (!has_device(&dev)) return fail(BAP_ECUDA, "no CUDA device");
+    TRY(preload_kernels(dev));
     bap_option* o = new (std::nothrow) bap_option();
     if (!o) return fail(BAP_ENOMEM, "host allocation");
     o->device = dev;
@@ -887,7 +942,10 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     int P2 = 1;
     while (P2 < J) P2 <<= 1;
     const size_t ab_smem = (size_t)J * 8 + std::max((size_t)P2 * 12, (size_t)J * 8) + (size_t)J + 16;
-    CU(cudaFuncSetAttribute(adaboost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(ab_smem, 48 * 1024)));
+    {
+        std::lock_guard<std::mutex> lk(g_fn_mu);
+        TRY(raise_smem_limit((const void*)adaboost_kernel, o->device, g_fn[{(const void*)adaboost_kernel, o->device}]));
+    }
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
         train_points_kernel<<<(J + 127) / 128, 128, 0, st>>>(
@@ -1385,16 +1443,7 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     const size_t smem = path_smem_bytes(a, rule, false, o->d);
     if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps = 1;
-    {
-        std::lock_guard<std::mutex> lk(g_fn_mu);
-        FnInfo& fi = g_fn[fn];
-        if (smem > fi.smem_set) {
-            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024)));
-            fi.smem_set = std::max<size_t>(smem, 48 * 1024);
-        }
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
-    }
-    if (bps < 1) bps = 1;
+    TRY(path_blocks_per_sm(fn, o->device, smem, &bps));
     long long blocks = (units + (kBlock / 32) - 1) / (kBlock / 32);
     blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
     void* args[] = {&a};

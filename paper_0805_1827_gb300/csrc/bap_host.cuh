@@ -159,6 +159,8 @@ struct bap_option {
 namespace bap {
 
 bap_status model_prepare(const bap_model* md, DevModel* out);
+// Loads every kernel of the library on `device` (the current device) once per process.
+bap_status preload_kernels(int device);
 bap_status option_alloc(bap_option** out);
 bap_status option_load(bap_option* o, const DevModel& hm);
 bap_status option_create(const bap_model* md, bap_option** out);

@@ -218,6 +218,7 @@ bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_ser
     int dev = 0, n = 0;
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0 || cudaGetDevice(&dev) != cudaSuccess)
         return fail(BAP_ECUDA, "no CUDA device");
+    TRY(preload_kernels(dev));
     bap_server* s = new (std::nothrow) bap_server();
     if (!s) return fail(BAP_ENOMEM, "host allocation");
     s->budget = device_mem_budget;
