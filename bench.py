@@ -5,7 +5,9 @@ One step = the whole hot path over one batch: for S0 in {90, 100, 110}, the Iban
 fit (5 boundaries x J=1024 Korobov points per date, N1 = 1e5 inner paths per continuation
 estimate, device Newton to |f| < 1e-6 or the x tolerance, FP64 quadratic regression, 8 fitted
 dates) and the final pricing with 1e6 paths (plus the FP64 re-run of the pricing that states
-the FP32 error).  value = inner + pricing path-steps actually simulated / device time.
+the FP32 error).  value = inner + pricing path-steps actually simulated / device time.  The
+Newton passes run in the cooperative form (one launch per date, --launch-mode); the JSON line
+also times the fit of one option in all three launch forms on the same seeds (launch_forms).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -257,6 +259,54 @@ def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
             "path_steps": steps}
 
 
+LAUNCH_MODES = {"plain": 0, "graph": 1, "coop": 2}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "path_kernel_5d_max_call.md")
+PATH_SOURCE = os.path.join(ROOT, "paper_0805_1827_gb300", "csrc", "bap_path.cuh")
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch of the dominant kernel, the cooperative Newton
+    launch, as ncu measured them on the full workload (profiles/path_kernel_5d_max_call.md);
+    None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        text = open(PROFILE_SUMMARY).read()
+        src = hashlib.sha256(open(PATH_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("source_sha256:", "dram_bytes_per_launch:")))
+    if fields.get("source_sha256", "").strip() != src:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def launch_forms(bap, params, stream) -> dict:
+    """The I&Z fit of the S0=100 option in each launch form on the same seeds (identical fits
+    and prices): one launch per Newton pass, one graph with conditional loops, one cooperative
+    launch per date.  Device time of the fit from the library's own events."""
+    out = {}
+    for name, mode in LAUNCH_MODES.items():
+        best = None
+        for rep in range(2):
+            o = bap.Option(spec_max_call(5, 100.0, rho=0.3), stream=stream.cuda_stream)
+            o.set_launch_mode(mode)
+            o.fit_boundary(params)
+            r = o.price(100_000, 5)
+            o.close()
+            if best is None or r["fit_ms"] < best["fit_ms"]:
+                best = r
+        out[name] = {"fit_ms": best["fit_ms"], "kernel_launches": best["kernel_launches"],
+                     "path_launches": best["path_launches"], "price": best["price"],
+                     "se": best["se"]}
+    prices = {v["price"] for v in out.values()}
+    out["identical_prices"] = len(prices) == 1
+    return out
+
+
 def run_ours(args) -> None:
     import torch
     import paper_0805_1827_gb300 as bap
@@ -273,7 +323,10 @@ def run_ours(args) -> None:
     stream = torch.cuda.current_stream()
     J = args.J or J_FULL
     N1 = args.N1 or N1_FULL
+    mode = LAUNCH_MODES[args.launch_mode]
     opts = [bap.Option(spec_max_call(5, s0, rho=0.3), stream=stream.cuda_stream) for s0 in S0S]
+    for o in opts:
+        o.set_launch_mode(mode)
     params = IZParams(J=J, N1=N1, degree=2, seed=1000 * rank + 1)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -343,6 +396,7 @@ def run_ours(args) -> None:
         for s0 in S0S:
             spec = spec_max_call(5, s0, rho=0.3)
             o = bap.Option(spec)
+            o.set_launch_mode(mode)
             o.fit_boundary(params)
             r = o.price(N_PRICE, 7)
             o.close()
@@ -358,6 +412,8 @@ def run_ours(args) -> None:
             torch.distributed.destroy_process_group()
         return
 
+    forms = launch_forms(bap, params, stream) if args.launch_forms else None
+
     ops = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -367,7 +423,9 @@ def run_ours(args) -> None:
             "achieved": achieved / 1e12 if achieved else None,
             "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": (achieved / peak_ops) if achieved else None,
-            "traffic": None,
+            "traffic": profiled_traffic(),
+            "traffic_basis": "ncu DRAM read+write bytes per cooperative Newton launch (full "
+                             "workload, profiles/path_kernel_5d_max_call.md)",
             "ops_per_path_step": ops["total"],
             "path_steps_per_s_in_kernel": tot_steps / (tot_kms / 1e3) if tot_kms > 0 else None,
             "peak_basis": (f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {sm_max:.0f} "
@@ -385,6 +443,7 @@ def run_ours(args) -> None:
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": tot_launch,
         "roofline": roof,
+        "launch_forms": forms,
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},
@@ -408,6 +467,10 @@ def main():
     ap.add_argument("--serving", type=int, default=512,
                     help="requests in the served-stream measurement (0: skip)")
     ap.add_argument("--max-inflight", type=int, default=32)
+    ap.add_argument("--launch-mode", default="coop", choices=sorted(LAUNCH_MODES),
+                    help="launch form of the I&Z Newton passes in the timed steps")
+    ap.add_argument("--no-launch-forms", dest="launch_forms", action="store_false",
+                    help="skip the side-by-side fit timing of the three launch forms")
     ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
     ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
     args = ap.parse_args()

@@ -155,7 +155,7 @@ bap_status bap_set_profiling(bap_option *opt, int on);
  * node whose body runs one Newton pass and then a one-thread kernel that continues the loop only
  * while points remain unconverged (at most max_iter passes), so the loop costs no host round
  * trip and no empty launches.  0: plain form, one launch per Newton pass up to max_iter per date
- * (also used while profiling is on).  If the graph cannot be built, the plain form is used.
+ * (the graph form falls back to it while profiling is on, and when the graph cannot be built).
  * 2: one cooperative launch per date runs all its Newton passes, a grid-wide barrier between
  * passes; the barrier's wait is bounded, and a barrier that times out makes the fit return
  * ECUDA.  All three forms give bitwise the same fit.  Errors: EINVAL (mode outside 0..2). */
@@ -243,7 +243,7 @@ bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_
 bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_server **out);
 
 /* Launch form of the I&Z fits the server runs (see bap_set_launch_mode).  Default 2 (one
- * cooperative launch per date, on at most 1/min(max_inflight, 8) of the device): each request
+ * cooperative launch per date, on at most 1/min(max_inflight, 4) of the device): each request
  * builds its fit once, so a graph's build and release cost more host time than its launches
  * save, and the plain form's max_iter launches per date fill the stream's launch queue. */
 bap_status bap_server_set_launch_mode(bap_server *srv, int mode);

@@ -874,7 +874,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
         TRY(enqueue_iz_prologue(o, p));
         for (int m = o->n_dates - 1; m >= 1; --m) {
             TRY(enqueue_iz_setup(o, p, m, false));
-            if (o->launch_mode == LAUNCH_COOP && !o->profiling)
+            if (o->launch_mode == LAUNCH_COOP)
                 TRY(enqueue_newton_coop(o, p, m, chunk, C));
             else
                 for (int it = 0; it < p->max_iter; ++it) TRY(enqueue_newton_pass(o, p, m, it, chunk, C));

@@ -84,7 +84,7 @@ bool start_request(bap_server* s, Request* r) {
     const auto t1 = Clock::now();
     if (st == BAP_OK) {
         r->opt->launch_mode = s->launch_mode;
-        r->opt->grid_share = std::min(s->max_inflight, 8);
+        r->opt->grid_share = std::min(s->max_inflight, 4);
     }
     if (st == BAP_OK)
         st = r->method == BAP_METHOD_IZ ? enqueue_fit_iz(r->opt, &r->iz) : enqueue_fit_cmc(r->opt, &r->cmc);
