@@ -161,6 +161,18 @@ bap_status bap_set_profiling(bap_option *opt, int on);
  * ECUDA.  All three forms give bitwise the same fit.  Errors: EINVAL (mode outside 0..2). */
 bap_status bap_set_launch_mode(bap_option *opt, int mode);
 
+/* How bap_fit_classifier runs the boosting of each date ([class], Section 3.2; the paper's
+ * sequential bottleneck).  1 (default): a thread-block cluster of d+1 blocks, one per feature,
+ * each sorting and scanning its feature while the blocks exchange per-round minima through
+ * distributed shared memory; used when the device can place such a cluster, else the one-block
+ * form.  0: one 1024-thread block for all features.  Both pick the stumps by the same rule on
+ * exact fixed-point errors.  Errors: EINVAL (null option, form outside 0..1). */
+bap_status bap_set_boost_form(bap_option *opt, int form);
+
+/* The form the last bap_fit_classifier ran (*form = 1 cluster, 0 one block).
+ * Errors: EINVAL (null argument). */
+bap_status bap_last_boost_form(const bap_option *opt, int *form);
+
 /* Ibanez-Zapatero fit (Algorithm 1 without [mc]): for m = N_T-1..1, boundary points by
  * device Newton on N1-path continuation estimates, then an FP64 least-squares boundary per
  * (date, boundary).  The fitted rule stays on the device.  Returns OK or ENOCONV. */

@@ -23,12 +23,14 @@ PURPOSE_IZ, PURPOSE_CMC, PURPOSE_TRAIN, PURPOSE_PRICE = 1, 2, 3, 4
 MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
 EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
+            "bap_set_boost_form", "bap_last_boost_form",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
             "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
             "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait",
             "bap_server_get_stats", "bap_server_destroy"]
 LAUNCH_PLAIN, LAUNCH_GRAPH, LAUNCH_COOP = 0, 1, 2
+BOOST_ONE_BLOCK, BOOST_CLUSTER = 0, 1
 METHOD_CODE = {"iz": 0, "cmc": 1}
 
 
@@ -92,6 +94,8 @@ def lib():
         L.bap_set_stream.argtypes = [vp, vp]
         L.bap_set_profiling.argtypes = [vp, C.c_int]
         L.bap_set_launch_mode.argtypes = [vp, C.c_int]
+        L.bap_set_boost_form.argtypes = [vp, C.c_int]
+        L.bap_last_boost_form.argtypes = [vp, C.POINTER(C.c_int)]
         L.bap_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
         L.bap_server_set_launch_mode.argtypes = [vp, C.c_int]
         L.bap_submit.argtypes = [vp, C.POINTER(_Model), C.c_int, vp, C.c_int64, C.c_uint64,
@@ -193,6 +197,14 @@ class Option:
 
     def set_launch_mode(self, mode: int):
         _check(lib().bap_set_launch_mode(self.h, mode))
+
+    def set_boost_form(self, form: int):
+        _check(lib().bap_set_boost_form(self.h, form))
+
+    def last_boost_form(self) -> int:
+        v = C.c_int(0)
+        _check(lib().bap_last_boost_form(self.h, C.byref(v)))
+        return v.value
 
     def fit_boundary(self, p) -> int:
         c = _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point, p.fp_eps)

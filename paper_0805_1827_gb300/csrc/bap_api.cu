@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <tuple>
 #include <vector>
 
 #include "bap_host.cuh"
@@ -679,6 +680,10 @@ bap_status preload_kernels(int device) {
         }
         const void* ab = (const void*)adaboost_kernel;
         TRY(raise_smem_limit(ab, device, g_fn[{ab, device}]));
+        const void* abc = (const void*)adaboost_cluster_kernel;
+        TRY(raise_smem_limit(abc, device, g_fn[{abc, device}]));
+        // d + 1 features up to 11 blocks per cluster: above the portable 8
+        CU(cudaFuncSetAttribute(abc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     }
     const void* others[] = {
         (const void*)iota_kernel,          (const void*)korobov_merit_kernel,
@@ -906,6 +911,41 @@ bap_status finish_fit_iz(bap_option* o) {
     return o->last_noconv > 0 ? BAP_ENOCONV : BAP_OK;
 }
 
+// Launch configuration of the cluster AdaBoost: one cluster of nF blocks of 512 threads.
+void boost_cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int nF, size_t smem,
+                          cudaStream_t st) {
+    cfg.gridDim = dim3((unsigned)nF);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nF;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
+// Whether a cluster of nF such blocks fits on the device (cached per device, nF and size).
+bap_status boost_cluster_fits(int device, int nF, size_t smem, cudaStream_t st, bool* ok) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, size_t>, bool> known;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(device, nF, smem);
+    auto it = known.find(key);
+    if (it == known.end()) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        boost_cluster_config(cfg, attr, nF, smem, st);
+        int n = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)adaboost_cluster_kernel, &cfg);
+        if (e != cudaSuccess) cudaGetLastError();
+        it = known.emplace(key, e == cudaSuccess && n >= 1).first;
+    }
+    *ok = it->second;
+    return BAP_OK;
+}
+
 bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
@@ -942,6 +982,12 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     int P2 = 1;
     while (P2 < J) P2 <<= 1;
     const size_t ab_smem = (size_t)J * 8 + std::max((size_t)P2 * 12, (size_t)J * 8) + (size_t)J + 16;
+    // the cluster form (one block per feature) when asked for and the device can place it
+    const size_t abc_smem = (size_t)J * 10 + std::max((size_t)P2 * 12, (size_t)J * 16) + 4 +
+                            8 * (size_t)((J + 31) / 32);
+    bool cluster = false;
+    if (o->boost_form == 1) TRY(boost_cluster_fits(o->device, nF, abc_smem, st, &cluster));
+    o->last_boost_cluster = cluster ? 1 : 0;
     {
         std::lock_guard<std::mutex> lk(g_fn_mu);
         TRY(raise_smem_limit((const void*)adaboost_kernel, o->device, g_fn[{(const void*)adaboost_kernel, o->device}]));
@@ -973,12 +1019,25 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         a.label_y = o->label_y.as<double>();
         a.label = o->label.as<int>();
         TRY(launch_path(o, a, R_CMC, false, (long long)n * C));
-        adaboost_kernel<<<1, 1024, ab_smem, st>>>(
-            o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label_y.as<double>(),
-            o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(),
-            o->err.as<double>(), o->max_stumps, o->n_stumps.as<int>(), o->feat.as<int>(),
-            o->thr.as<double>(), o->pol.as<int>(), o->alpha.as<double>(), o->rec_len,
-            o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
+        if (cluster) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            boost_cluster_config(cfg, attr, nF, abc_smem, st);
+            CU(cudaLaunchKernelEx(&cfg, adaboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
+                                  m, J, (const double*)o->start.as<double>(),
+                                  (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
+                                  o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
+                                  o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+                                  o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
+                                  o->rec_d.as<double>(), o->fitted.as<int>()));
+        } else {
+            adaboost_kernel<<<1, 1024, ab_smem, st>>>(
+                o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label_y.as<double>(),
+                o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(),
+                o->err.as<double>(), o->max_stumps, o->n_stumps.as<int>(), o->feat.as<int>(),
+                o->thr.as<double>(), o->pol.as<int>(), o->alpha.as<double>(), o->rec_len,
+                o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
+        }
         ++o->launches;
         CU(cudaGetLastError());
         TRY(record_diag(o, m, false));
@@ -1106,6 +1165,19 @@ bap_status bap_set_launch_mode(bap_option* o, int mode) {
     if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH && mode != LAUNCH_COOP)
         return fail(BAP_EINVAL, "bad launch mode");
     o->launch_mode = mode;
+    return BAP_OK;
+}
+
+bap_status bap_set_boost_form(bap_option* o, int form) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    if (form != 0 && form != 1) return fail(BAP_EINVAL, "boost form outside 0..1");
+    o->boost_form = form;
+    return BAP_OK;
+}
+
+bap_status bap_last_boost_form(const bap_option* o, int* form) {
+    if (!o || !form) return fail(BAP_EINVAL, "null argument");
+    *form = o->last_boost_cluster;
     return BAP_OK;
 }
 

@@ -5,6 +5,8 @@
 
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 namespace bap {
 
 // ---------------------------------------------------------------------------------------------
@@ -442,6 +444,23 @@ __device__ inline bool key_less(double a, int ia, double b, int ib) {
 
 constexpr double kFix = 1152921504606846976.0;   // 2^60
 
+// round(v * 2^60) to the nearest integer, ties to even, for 0 <= v <= 1: the same value as
+// __double2ll_rn(v * 2^60) (the product is exact), from the bits of v with integer operations
+// only.  v = s * 2^(e - 1075) with the 53-bit significand s, so v * 2^60 = s * 2^(e - 1015).
+__device__ __forceinline__ long long fix60(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;                                  // zero or subnormal: rounds to 0
+    const unsigned long long s = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1015 - e;                               // right shift of s
+    if (sh <= 0) return (long long)(s << (-sh));           // exact (v >= 2^-7: sh >= -8)
+    if (sh >= 64) return 0;                                // below 2^-64 of a unit: 0
+    const unsigned long long q = s >> sh;
+    const unsigned long long rem = s & ((1ull << sh) - 1);
+    const unsigned long long half = 1ull << (sh - 1);
+    return (long long)(q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0));
+}
+
 // Block-wide exclusive scan of two 64-bit values per thread (1024 threads); returns the block
 // totals through tot_a / tot_b.  Uses red_a / red_b (32 entries each) in shared memory.
 __device__ inline void block_scan2(long long& a, long long& b, long long* red_a, long long* red_b,
@@ -497,6 +516,50 @@ __device__ inline double block_sum_d(double v, double* red) {
     return r;
 }
 
+// Feature f of training point i: the d prices, then the payoff Phi in FP64 (the same
+// definition as the label epilogue of the path kernel).
+__device__ inline double cmc_feature(const DevModel* M, const double* X, int i, int f) {
+    const int d = M->d;
+    if (f < d) return X[(size_t)i * d + f];
+    const double* S = X + (size_t)i * d;
+    double v;
+    if (M->payoff == BAP_MAX_CALL) {
+        double mx = S[0];
+        for (int q = 1; q < d; ++q) mx = S[q] > mx ? S[q] : mx;
+        v = mx - M->K;
+    } else if (M->payoff == BAP_BASKET_PUT) {
+        double b = 0;
+        for (int q = 0; q < d; ++q) b += M->w[q] * S[q];
+        v = M->K - b;
+    } else {
+        double lg = 0;
+        for (int q = 0; q < d; ++q) lg += M->w[q] * log(S[q]);
+        v = exp(lg) - M->K;
+    }
+    return v > 0 ? v : 0;
+}
+
+// Bitonic sort of (key, idx) pairs over P2 entries in shared memory, by (value, index).
+__device__ inline void block_bitonic(double* key, int* idx, int P2) {
+    const int tid = threadIdx.x;
+    for (int size = 2; size <= P2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < P2; i += blockDim.x) {
+                const int jx = i ^ stride;
+                if (jx > i) {
+                    const bool up = (i & size) == 0;
+                    const bool lt = key_less(key[jx], idx[jx], key[i], idx[i]);
+                    if (lt == up) {
+                        const double tk = key[i]; key[i] = key[jx]; key[jx] = tk;
+                        const int ti = idx[i]; idx[i] = idx[jx]; idx[jx] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void __launch_bounds__(1024) adaboost_kernel(
     const DevModel* M, int m, int J, const double* X, const double* label_y, const int* label,
     int n_rounds, double* sorted_v, int* sorted_i, double* err, int max_stumps, int* n_stumps,
@@ -527,51 +590,11 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
     // definition as the label epilogue of the path kernel)
     for (int f = 0; f < nF; ++f) {
         for (int i = tid; i < P2; i += blockDim.x) {
-            if (i < J) {
-                double v;
-                if (f < d) {
-                    v = X[(size_t)i * d + f];
-                } else {
-                    const double* S = X + (size_t)i * d;
-                    if (M->payoff == BAP_MAX_CALL) {
-                        double mx = S[0];
-                        for (int q = 1; q < d; ++q) mx = S[q] > mx ? S[q] : mx;
-                        v = mx - M->K;
-                    } else if (M->payoff == BAP_BASKET_PUT) {
-                        double b = 0;
-                        for (int q = 0; q < d; ++q) b += M->w[q] * S[q];
-                        v = M->K - b;
-                    } else {
-                        double lg = 0;
-                        for (int q = 0; q < d; ++q) lg += M->w[q] * log(S[q]);
-                        v = exp(lg) - M->K;
-                    }
-                    v = v > 0 ? v : 0;
-                }
-                key[i] = v;
-                idx[i] = i;
-            } else {
-                key[i] = INFINITY;
-                idx[i] = 0x7fffffff;
-            }
+            key[i] = i < J ? cmc_feature(M, X, i, f) : INFINITY;
+            idx[i] = i < J ? i : 0x7fffffff;
         }
         __syncthreads();
-        for (int size = 2; size <= P2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < P2; i += blockDim.x) {
-                    const int jx = i ^ stride;
-                    if (jx > i) {
-                        const bool up = (i & size) == 0;
-                        const bool lt = key_less(key[jx], idx[jx], key[i], idx[i]);
-                        if (lt == up) {
-                            const double tk = key[i]; key[i] = key[jx]; key[jx] = tk;
-                            const int ti = idx[i]; idx[i] = idx[jx]; idx[jx] = ti;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        block_bitonic(key, idx, P2);
         for (int i = tid; i < J; i += blockDim.x) {
             sorted_v[(size_t)f * J + i] = key[i];
             sorted_i[(size_t)f * J + i] = idx[i];
@@ -594,7 +617,7 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
         // fixed-point weights and their total
         long long part = 0;
         for (int i = tid; i < J; i += blockDim.x) {
-            const long long v = __double2ll_rn(w[i] * kFix);
+            const long long v = fix60(w[i]);
             wf[i] = v;
             part += v;
         }
@@ -717,6 +740,267 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
                       rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
         fitted[m] = 1;
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// [class] The same AdaBoost fit on a thread-block cluster: block f (cluster rank f) owns feature
+// f, so the per-feature sorts, prefix scans and error searches of a round run on nF SMs at once.
+// Every block keeps its own copy of the weights and applies the same update in the same order,
+// so the copies stay identical.  Per round the blocks exchange, through the distributed shared
+// memory of the leader block (rank 0): the least error of each feature, then the first
+// candidate of each feature within the tolerance and its error and threshold.  Two cluster
+// barriers per round; every decision is taken from values read back from the leader, so all
+// blocks take the same branches and meet the same barriers.  Choices, tie rule and update are
+// those of adaboost_kernel.
+
+struct BoostExchange {
+    long long W;                   // fixed-point total weight of the round (the leader's)
+    long long fmin[MAXF];          // least error per feature
+    long long cand[MAXF];          // first candidate code per feature within the tolerance
+    long long cerr[MAXF];          // its error
+    double cthr[MAXF];             // its threshold
+};
+
+__global__ void __launch_bounds__(512) adaboost_cluster_kernel(
+    const DevModel* M, int m, int J, const double* X, const int* label, int n_rounds,
+    double* sorted_v, int* sorted_i, int max_stumps, int* n_stumps, int* feat, double* thr,
+    int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d, int* fitted) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned FULL = 0xffffffffu;
+    const int d = M->d;
+    const int nF = d + 1;
+    const int f = (int)cluster.block_rank();            // the feature of this block
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    const int nwords = (J + 31) / 32;
+    // shared memory: w | region (sort keys, then wf, six, inv) | lab | split | mask | cmask
+    double* w = reinterpret_cast<double*>(smem);                          // J
+    unsigned char* region = smem + (size_t)J * 8;
+    double* key = reinterpret_cast<double*>(region);                      // P2 (sort)
+    int* idx = reinterpret_cast<int*>(key + P2);                          // P2 (sort)
+    long long* wf = reinterpret_cast<long long*>(region);                 // J fixed-point weights
+    int* six = reinterpret_cast<int*>(region + (size_t)J * 8);           // J: sorted position -> point
+    int* inv = six + J;                                                    // J: point -> sorted position
+    const size_t region_bytes = (size_t)P2 * 12 > (size_t)J * 16 ? (size_t)P2 * 12 : (size_t)J * 16;
+    signed char* lab = reinterpret_cast<signed char*>(region + region_bytes);   // J
+    unsigned char* split = reinterpret_cast<unsigned char*>(lab + J);     // J: a threshold after r
+    unsigned* mask = reinterpret_cast<unsigned*>(smem + ((size_t)J * 8 + region_bytes + 2 * (size_t)J + 3) / 4 * 4);
+    unsigned* cmask = mask + nwords;                                       // the chosen stump's
+    __shared__ BoostExchange ex;                         // read remotely on the leader only
+    __shared__ long long red_a[32], red_b[32];
+    __shared__ double red_d[32];
+    __shared__ long long s_min, s_cand, s_lim, s_W;
+    __shared__ double s_thr, s_alpha, s_fok, s_fbad;
+    __shared__ int s_f, s_pol, s_stop;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    BoostExchange* lead = cluster.map_shared_rank(&ex, 0);
+
+    // sort this block's feature and publish it; keep the permutation both ways, and where the
+    // sorted values step (a threshold can sit after position r), in shared memory
+    for (int i = tid; i < P2; i += blockDim.x) {
+        key[i] = i < J ? cmc_feature(M, X, i, f) : INFINITY;
+        idx[i] = i < J ? i : 0x7fffffff;
+    }
+    __syncthreads();
+    block_bitonic(key, idx, P2);
+    for (int r = tid; r < J; r += blockDim.x) {
+        sorted_v[(size_t)f * J + r] = key[r];
+        sorted_i[(size_t)f * J + r] = idx[r];
+        split[r] = (r < J - 1 && key[r + 1] > key[r]) ? 1 : 0;
+    }
+    __syncthreads();
+    for (int r = tid; r < J; r += blockDim.x) {
+        const int k = sorted_i[(size_t)f * J + r];
+        six[r] = k;
+        inv[k] = r;
+    }
+    for (int i = tid; i < J; i += blockDim.x) {
+        w[i] = 1.0 / (double)J;
+        wf[i] = fix60(w[i]);
+        lab[i] = label[i] > 0 ? 1 : -1;
+    }
+    __threadfence();          // the sorted features are read by every block of the cluster
+    cluster.sync();
+
+    const int per = (J + blockDim.x - 1) / blockDim.x;
+    const int lo = tid * per, hi = min(J, lo + per);
+    const long long tol = (long long)(1e-12 * kFix);
+    const size_t o_st = (size_t)m * max_stumps;
+    int count = 0;
+    for (int round = 0; round < n_rounds; ++round) {
+        if (tid == 0) s_min = LLONG_MAX;
+        // prefix of this feature's positive and negative weights over the sorted order; the two
+        // totals give the round's total weight exactly
+        long long sp = 0, sn = 0;
+        for (int r = lo; r < hi; ++r) {
+            const int k = six[r];
+            if (lab[k] > 0) sp += wf[k]; else sn += wf[k];
+        }
+        long long pp0 = sp, pn0 = sn, tot_p = 0, tot_n = 0;
+        block_scan2(pp0, pn0, red_a, red_b, tot_p, tot_n);
+        const long long W = tot_p + tot_n;
+        const long long neg = tot_n;
+        long long my = min(neg, W - neg);
+        {
+            long long pp = pp0, pn = pn0;
+            for (int r = lo; r < hi; ++r) {
+                const int k = six[r];
+                if (lab[k] > 0) pp += wf[k]; else pn += wf[k];
+                if (split[r]) {
+                    const long long e = pp + (neg - pn);
+                    my = min(my, min(e, W - e));
+                }
+            }
+        }
+        atomicMin(&s_min, my);
+        __syncthreads();
+        if (tid == 0) {
+            lead->fmin[f] = s_min;
+            if (f == 0) ex.W = W;
+        }
+        cluster.sync();
+        // the first candidate of this feature within the tolerance of the overall least error
+        if (tid == 0) {
+            long long emin = LLONG_MAX;
+            for (int g = 0; g < nF; ++g) emin = min(emin, lead->fmin[g]);
+            s_lim = emin + tol;
+            s_W = lead->W;
+            s_cand = LLONG_MAX;
+        }
+        __syncthreads();
+        const long long Wl = s_W;
+        const long long lim = s_lim;
+        long long c = LLONG_MAX;
+        if (neg <= lim) c = 0;
+        else if (W - neg <= lim) c = 1;
+        else {
+            long long pp = pp0, pn = pn0;
+            for (int r = lo; r < hi && c == LLONG_MAX; ++r) {
+                const int k = six[r];
+                if (lab[k] > 0) pp += wf[k]; else pn += wf[k];
+                if (!split[r]) continue;
+                const long long e = pp + (neg - pn);
+                if (e <= lim) c = 2 + 2LL * r;
+                else if (W - e <= lim) c = 3 + 2LL * r;
+            }
+        }
+        if (c != LLONG_MAX) atomicMin(&s_cand, c);
+        __syncthreads();
+        const long long cmin = s_cand;
+        if (cmin < 2 || cmin == LLONG_MAX ? tid == 0 : c == cmin) {
+            // thread 0 for a constant stump or no candidate; else the one thread whose
+            // segment holds the threshold
+            long long e = 0;
+            double th = -INFINITY;
+            if (cmin == 0) e = neg;
+            else if (cmin == 1) e = W - neg;
+            else if (cmin != LLONG_MAX) {
+                const int r0 = (int)((cmin - 2) / 2);
+                long long pp = pp0, pn = pn0;
+                for (int r = lo; r <= r0; ++r) {
+                    const int k = six[r];
+                    if (lab[k] > 0) pp += wf[k]; else pn += wf[k];
+                }
+                const long long ep = pp + (neg - pn);
+                e = ((cmin - 2) % 2 == 0) ? ep : W - ep;
+                th = 0.5 * (sorted_v[(size_t)f * J + r0] + sorted_v[(size_t)f * J + r0 + 1]);
+            }
+            lead->cand[f] = cmin;
+            lead->cerr[f] = e;
+            lead->cthr[f] = th;
+        }
+        // which points lie above this feature's candidate threshold, one bit per point (read by
+        // every block if this feature's stump is chosen)
+        {
+            const int rstar = cmin >= 2 && cmin != LLONG_MAX ? (int)((cmin - 2) / 2) : -1;
+            for (int wd = warp; wd < nwords; wd += nwarps) {
+                const int i = wd * 32 + lane;
+                const bool above = i < J && inv[i] > rstar;
+                const unsigned bits = __ballot_sync(FULL, above);
+                if (lane == 0) mask[wd] = bits;
+            }
+        }
+        cluster.sync();
+        // the chosen stump: the first feature with a candidate.  Thread 0 of every block reads
+        // the same leader values and takes the same decision; FP64 log/exp once per block.
+        if (tid == 0) {
+            int cf = -1;
+            long long cc = 0;
+            for (int g = 0; g < nF && cf < 0; ++g) {
+                const long long v = lead->cand[g];
+                if (v != LLONG_MAX) { cf = g; cc = v; }
+            }
+            const int fs0 = cf < 0 ? 0 : cf;
+            long long e;
+            double th0;
+            int pl0;
+            if (cf < 0) {
+                th0 = -INFINITY; pl0 = 1; e = Wl;     // no candidate at all: stop below
+            } else {
+                e = lead->cerr[fs0];
+                th0 = lead->cthr[fs0];
+                pl0 = (cc < 2) ? (cc == 0 ? 1 : -1) : (((cc - 2) % 2 == 0) ? 1 : -1);
+            }
+            const double eps = (double)e / (double)Wl;
+            s_stop = 0;
+            if (eps >= 0.5 - 1e-12) {
+                s_stop = 1;
+            } else {
+                const double ec = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);
+                const double al = 0.5 * log((1.0 - ec) / ec);
+                s_f = fs0; s_thr = th0; s_pol = pl0; s_alpha = al;
+                s_fok = exp(-al);
+                s_fbad = exp(al);
+                if (eps <= 1e-10) s_stop = 2;
+            }
+        }
+        __syncthreads();
+        if (s_stop == 1) break;
+        const int fs = s_f;
+        const int pl = s_pol;
+        if (f == 0 && tid == 0) {
+            feat[o_st + count] = fs;
+            thr[o_st + count] = s_thr;
+            pol[o_st + count] = pl;
+            alpha[o_st + count] = s_alpha;
+        }
+        ++count;
+        {
+            const unsigned* src = cluster.map_shared_rank(mask, fs);
+            for (int wd = tid; wd < nwords; wd += blockDim.x) cmask[wd] = src[wd];
+        }
+        __syncthreads();
+        // w_i <- w_i exp(-alpha y_i h(x_i)), normalise, and the next round's fixed-point weights
+        // (the same order in every block)
+        {
+            const double fok = s_fok, fbad = s_fbad;
+            double part2 = 0.0;
+            for (int i = tid; i < J; i += blockDim.x) {
+                const int h = ((cmask[i >> 5] >> (i & 31)) & 1u) ? pl : -pl;
+                const double nw = w[i] * (h == lab[i] ? fok : fbad);
+                w[i] = nw;
+                part2 += nw;
+            }
+            const double Wn = block_sum_d(part2, red_d);
+            const double invW = 1.0 / Wn;
+            for (int i = tid; i < J; i += blockDim.x) {
+                const double v = w[i] * invW;
+                w[i] = v;
+                wf[i] = fix60(v);
+            }
+            __syncthreads();
+        }
+        if (s_stop == 2) break;
+    }
+    if (f == 0 && tid == 0) {
+        n_stumps[m] = count;
+        stage_cmc_one(nF, count, feat + o_st, thr + o_st, pol + o_st, alpha + o_st, rec_len,
+                      rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
+        fitted[m] = 1;
+    }
+    cluster.sync();           // the leader's exchange area and the masks stay until all are done
 }
 
 // ---------------------------------------------------------------------------------------------

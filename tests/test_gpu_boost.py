@@ -1,0 +1,90 @@
+"""CMC boosting on a thread-block cluster (one block per feature) against the one-block form and
+the oracle's AdaBoost (needs a CUDA device).
+
+Both device forms choose stumps by the same rule on exact fixed-point errors; only the FP64
+normalisation of the weights is summed in another order, so stumps agree exactly in feature and
+polarity and to rounding in threshold and alpha.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_0805_1827_gb300 as bap
+from bap_workloads import CMCParams, PURPOSE_CMC, spec_basket_put_7, spec_max_call, spec_put_1d
+
+pytestmark = pytest.mark.gpu
+
+
+def _stumps(opt, spec):
+    buf = opt.export_rules()
+    nd = spec.n_dates + 1
+    ms = int(buf[5])
+    off = 6 + nd
+    quad = buf[off:off + nd * ms * 4].reshape(nd, ms, 4)
+    nst = buf[off + nd * ms * 4: off + nd * ms * 4 + nd].astype(int)
+    return quad, nst
+
+
+def _fit(spec, params, form):
+    o = bap.Option(spec)
+    o.set_boost_form(form)
+    o.fit_classifier(params)
+    return o
+
+
+@pytest.mark.parametrize("spec,params", [
+    (spec_basket_put_7(0), CMCParams(J=400, N2=1000, n_stumps=40, seed=5)),
+    (spec_max_call(10, 100.0, rho=0.3, n_dates=4, T=1.0), CMCParams(J=300, N2=500, n_stumps=30, seed=2)),
+    (spec_put_1d(n_dates=6), CMCParams(J=257, N2=800, n_stumps=25, seed=9)),
+])
+def test_cluster_and_one_block_boosting_agree(spec, params):
+    a = _fit(spec, params, bap.BOOST_ONE_BLOCK)
+    b = _fit(spec, params, bap.BOOST_CLUSTER)
+    assert a.last_boost_form() == 0
+    assert b.last_boost_form() == 1          # d + 1 <= 11 blocks fit on a GB300
+    qa, na = _stumps(a, spec)
+    qb, nb = _stumps(b, spec)
+    assert np.array_equal(na, nb)
+    for m in range(1, spec.n_dates):
+        for i in range(na[m]):
+            fa, ta, pa, aa = qa[m, i]
+            fb, tb, pb, ab = qb[m, i]
+            assert (fa, pa) == (fb, pb), (m, i)
+            assert (math.isinf(ta) and math.isinf(tb)) or abs(ta - tb) <= 1e-12 * max(1.0, abs(ta))
+            assert abs(aa - ab) <= 1e-9 * max(1.0, abs(aa)), (m, i, aa, ab)
+    ra, rb = a.price(100_000, 3), b.price(100_000, 3)
+    assert ra["price"] == rb["price"] and ra["var"] == rb["var"]
+    a.close()
+    b.close()
+
+
+def test_cluster_boosting_matches_oracle_adaboost_on_gpu_labels():
+    """The oracle's AdaBoost on the GPU's own training points and labels of every date gives the
+    cluster form's stumps."""
+    spec = spec_basket_put_7(0)
+    params = CMCParams(J=600, N2=800, n_stumps=60, seed=11)
+    opt = _fit(spec, params, bap.BOOST_CLUSTER)
+    assert opt.last_boost_form() == 1
+    quad, nst = _stumps(opt, spec)
+    for m in range(1, spec.n_dates):
+        y, _, _ = opt.fit_points(m)
+        X = oracle.train_points(spec, m, params.J, params.seed)
+        Fx = np.concatenate([X, oracle.payoff(spec, X)[:, None]], axis=1)
+        st = oracle.adaboost(Fx, np.where(y > 0, 1, -1), params.n_stumps)
+        assert nst[m] == len(st), m
+        for i, (f, thr, pol, al) in enumerate(st):
+            gf, gt, gp, ga = quad[m, i]
+            assert (int(gf), int(gp)) == (f, pol), (m, i)
+            assert (math.isinf(thr) and math.isinf(gt)) or abs(gt - thr) <= 1e-9 * max(1, abs(thr))
+            assert abs(ga - al) <= 1e-8 * max(1.0, abs(al)), (m, i)
+    opt.close()
+
+
+def test_boost_form_argument_checks():
+    opt = bap.Option(spec_put_1d(n_dates=3))
+    with pytest.raises(bap.BapError) as e:
+        opt.set_boost_form(2)
+    assert e.value.status == bap.BAP_EINVAL
+    opt.close()
