@@ -348,6 +348,44 @@ def cmc_boost_forms(bap, stream) -> dict:
     return out
 
 
+def paper_tables(bap) -> dict:
+    """The paper's 3-asset max-call (Eq. 2 / Eq. 3) at its own settings: Table 1 (I&Z, J=128,
+    N1=5e3), Table 2 (J sweep), Table 3 (N1 sweep), Table 4 (CMC, 5e3 points, N2=500, 200
+    stumps), N=1e6 pricing paths; our price, SE and fit time beside the printed price, the
+    printed binomial value and the printed minutes on 16 processors."""
+    from bap_workloads import CMCParams
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")))
+
+    def run(s0, params):
+        o = bap.Option(spec_max_call(3, float(s0)))
+        if isinstance(params, IZParams):
+            o.fit_boundary(params)
+        else:
+            o.fit_classifier(params)
+        r = o.price(1_000_000, 2)
+        o.close()
+        return {"price": r["price"], "se": r["se"], "fit_ms": r["fit_ms"], "price_ms": r["price_ms"]}
+
+    out = {"table1_iz": {}, "table2_iz_J": {}, "table3_iz_N1": {}, "table4_cmc": {}}
+    for s0 in (90, 100, 110):
+        g = gold["table1_iz"][str(s0)]
+        out["table1_iz"][s0] = {**run(s0, IZParams(J=128, N1=5000, degree=2, seed=1)),
+                                "paper_price": g["price"], "binomial": g["binomial"]}
+    for J in (128, 256, 1024):
+        g = gold["table2_iz_J"][str(J)]
+        out["table2_iz_J"][J] = {**run(90, IZParams(J=J, N1=5000, degree=2, seed=1)),
+                                 "paper_price": g["price"], "paper_minutes_16_procs": g["minutes_16_procs"]}
+    for N1 in (5000, 10_000, 100_000):
+        g = gold["table3_iz_N1"][str(N1)]
+        out["table3_iz_N1"][N1] = {**run(90, IZParams(J=128, N1=N1, degree=2, seed=1)),
+                                   "paper_price": g["price"], "paper_minutes_16_procs": g["minutes_16_procs"]}
+    for s0 in (90, 100, 110):
+        g = gold["table4_cmc"][str(s0)]
+        out["table4_cmc"][s0] = {**run(s0, CMCParams(J=5000, N2=500, n_stumps=200, seed=1)),
+                                 "paper_price": g["price"], "binomial": g["binomial"]}
+    return out
+
+
 def run_ours(args) -> None:
     import torch
     import paper_0805_1827_gb300 as bap
@@ -447,6 +485,7 @@ def run_ours(args) -> None:
 
     forms = launch_forms(bap, params, stream) if args.launch_forms else None
     boost = cmc_boost_forms(bap, stream) if args.launch_forms else None
+    tables = paper_tables(bap) if args.paper_tables else None
 
     ops = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
@@ -479,6 +518,7 @@ def run_ours(args) -> None:
         "roofline": roof,
         "launch_forms": forms,
         "cmc_boost_forms": boost,
+        "paper_tables": tables,
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},
@@ -506,6 +546,8 @@ def main():
                     help="launch form of the I&Z Newton passes in the timed steps")
     ap.add_argument("--no-launch-forms", dest="launch_forms", action="store_false",
                     help="skip the side-by-side fit timings (I&Z launch forms, CMC boosting forms)")
+    ap.add_argument("--no-paper-tables", dest="paper_tables", action="store_false",
+                    help="skip the paper's Tables 1-4 workloads")
     ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
     ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
     args = ap.parse_args()
