@@ -89,6 +89,8 @@ class CMCParams:
     N2: int = 2000
     n_stumps: int = 200
     seed: int = 0
+    sampler: int = 0          # training points: 0 independent per date, 1 Brownian bridge back
+                              # from the last fitted date (Section 3.3)
 
 
 def equicorrelation(d: int, rho: float) -> np.ndarray:

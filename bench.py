@@ -386,6 +386,29 @@ def paper_tables(bap) -> dict:
     return out
 
 
+def root_find_study(bap) -> dict:
+    """Safeguarded Newton against the paper's literal fixed-point iteration (eps = 0.01) on the
+    Table 1 workload (3-asset max-call, S0=90, J=128, N1=5e3, 8 fitted dates, max_iter 100):
+    continuation evaluations per boundary point (mean, median, p90, max: the load imbalance
+    among points), points without convergence, inner path-steps, fit time and price."""
+    import numpy as np
+    out = {}
+    for name, fp in (("newton", 0), ("fixed_point", 1)):
+        spec = spec_max_call(3, 90.0)
+        o = bap.Option(spec)
+        p = IZParams(J=128, N1=5000, degree=2, seed=1, fixed_point=fp, fp_eps=0.01, max_iter=100)
+        o.fit_boundary(p)
+        r = o.price(1_000_000, 2)
+        its = np.concatenate([o.fit_points(m)[1] for m in range(1, spec.n_dates)])
+        o.close()
+        out[name] = {"evals_mean": float(its.mean()), "evals_p50": float(np.percentile(its, 50)),
+                     "evals_p90": float(np.percentile(its, 90)), "evals_max": int(its.max()),
+                     "points": int(its.size), "noconv": r["n_noconv"],
+                     "fit_path_steps": r["fit_path_steps"], "fit_ms": r["fit_ms"],
+                     "price": r["price"], "se": r["se"]}
+    return out
+
+
 def run_ours(args) -> None:
     import torch
     import paper_0805_1827_gb300 as bap
@@ -486,6 +509,7 @@ def run_ours(args) -> None:
     forms = launch_forms(bap, params, stream) if args.launch_forms else None
     boost = cmc_boost_forms(bap, stream) if args.launch_forms else None
     tables = paper_tables(bap) if args.paper_tables else None
+    rootfind = root_find_study(bap) if args.paper_tables else None
 
     ops = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
@@ -519,6 +543,7 @@ def run_ours(args) -> None:
         "launch_forms": forms,
         "cmc_boost_forms": boost,
         "paper_tables": tables,
+        "root_find_study": rootfind,
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},
@@ -547,7 +572,7 @@ def main():
     ap.add_argument("--no-launch-forms", dest="launch_forms", action="store_false",
                     help="skip the side-by-side fit timings (I&Z launch forms, CMC boosting forms)")
     ap.add_argument("--no-paper-tables", dest="paper_tables", action="store_false",
-                    help="skip the paper's Tables 1-4 workloads")
+                    help="skip the paper's Tables 1-4 workloads and the root-finding study")
     ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
     ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
     args = ap.parse_args()

@@ -100,6 +100,10 @@ typedef struct bap_cmc_params {
     int64_t N2;               /* inner paths per training point, >= 1 */
     int n_stumps;             /* boosting rounds per date, 1..BAP_MAX_STUMPS */
     uint64_t seed;
+    int sampler;              /* training points: 0 independent draws from the law of S_{t_m}
+                                 per date; 1 one set of J points walked back from the last
+                                 fitted date by a Brownian bridge (Section 3.3), each date's
+                                 bridge normals being those the independent draw would use */
 } bap_cmc_params;
 
 typedef struct bap_result {

@@ -113,6 +113,9 @@ def _lib(precision: str = "f64"):
                                       C.POINTER(C.c_double), i64p]
             lib.orc_train_points.argtypes = [mp, C.c_int, C.c_int, C.c_uint64, C.c_int,
                                              C.POINTER(C.c_double)]
+            lib.orc_train_points_bridge.argtypes = [mp, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                                    C.POINTER(C.c_double)]
             lib.orc_exercise.argtypes = [mp, rp, C.c_int, C.c_int, C.POINTER(C.c_double),
                                          C.POINTER(C.c_int)]
             _LIBS[precision] = lib
@@ -512,6 +515,21 @@ def train_points(spec: OptionSpec, m: int, J: int, seed: int, precision: str = "
     return X
 
 
+def train_points_bridge(spec: OptionSpec, m: int, J: int, seed: int, W_next=None,
+                        precision: str = "f64"):
+    """Training points of date m walked back from those of date m+1 by a Brownian bridge
+    (Section 3.3); W_next = the driving Brownian motion at t_{m+1} (None at the last fitted
+    date, where the draw is the independent one).  Returns (W_m, X_m)."""
+    W = np.zeros((J, spec.d))
+    X = np.zeros((J, spec.d))
+    wn = None if W_next is None else _dp(np.ascontiguousarray(W_next, dtype=np.float64))
+    rc = _lib(precision).orc_train_points_bridge(C.byref(Model(spec).c), m, PURPOSE_TRAIN, seed,
+                                                 J, wn, _dp(W), _dp(X))
+    if rc:
+        raise ValueError("orc_train_points_bridge rejected its arguments")
+    return W, X
+
+
 def stump_predict(Fx: np.ndarray, feat: int, thr: float, pol: int) -> np.ndarray:
     return np.where(Fx[:, feat] > thr, pol, -pol)
 
@@ -578,8 +596,12 @@ def cmc_fit(spec: OptionSpec, params: CMCParams, n_threads: int = 0, precision: 
     dates = range(spec.n_dates - 1, 0, -1)
     if last_date_only:
         dates = [spec.n_dates - 1]
+    W = None
     for m in dates:
-        X = train_points(spec, m, params.J, params.seed, precision)
+        if getattr(params, "sampler", 0) == 1:
+            W, X = train_points_bridge(spec, m, params.J, params.seed, W, precision)
+        else:
+            X = train_points(spec, m, params.J, params.seed, precision)
         ids = np.arange(params.J, dtype=np.int32)
         sums, steps = continuation(spec, rules, m, PURPOSE_CMC, params.seed, ids, X, params.N2,
                                    None, n_threads, precision)

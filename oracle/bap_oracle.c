@@ -515,6 +515,44 @@ int orc_train_points(const orc_model *M, int m, int purpose, uint64_t seed, int 
     return 0;
 }
 
+/* CMC training points walked back by a Brownian bridge (Section 3.3: the points of date m are
+ * simulated backward from those of date m+1).  W is the d-dimensional Brownian motion with
+ * covariance rho t that drives log S^q = log S_0^q + mu_q t + sigma_q W^q.  At the last fitted
+ * date (Wnext == NULL) W_m = sqrt(t_m) L z, the independent draw; before it, given W at t_{m+1},
+ *     W_m = (t_m / t_{m+1}) W_{m+1} + sqrt(t_m (t_{m+1} - t_m) / t_{m+1}) L z,
+ * the conditional law of a Brownian motion pinned at 0 at t_0 = 0 and at W_{m+1} at t_{m+1}.
+ * z are the same normals as the independent draw of date m (counter (j, 0, c, 0), key of m).
+ * Writes W_m (J x d) and the prices X (J x d). */
+int orc_train_points_bridge(const orc_model *M, int m, int purpose, uint64_t seed, int J,
+                            const double *Wnext, double *W, double *X)
+{
+    if (M->d < 1 || M->d > ORC_MAXD || m < 1 || m > M->n_dates) return 1;
+    if (Wnext && m + 1 > M->n_dates) return 1;
+    int d = M->d;
+    uint32_t key[2];
+    make_key(seed, purpose, m, key);
+    double tm = M->t[m];
+    double a = 0.0, b = sqrt(tm);
+    if (Wnext) {
+        double tn = M->t[m + 1];
+        a = tm / tn;
+        b = sqrt(tm * (tn - tm) / tn);
+    }
+    for (int j = 0; j < J; ++j) {
+        real z[ORC_MAXD];
+        normals(key, (uint32_t)j, 0u, 0u, d, z);
+        for (int q = 0; q < d; ++q) {
+            double lz = 0;
+            for (int i = 0; i <= q; ++i) lz += M->L[q * d + i] * (double)z[i];
+            double w = b * lz + (Wnext ? a * Wnext[(size_t)j * d + q] : 0.0);
+            double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+            W[(size_t)j * d + q] = w;
+            X[(size_t)j * d + q] = M->S0[q] * exp(mu * tm + M->sigma[q] * w);
+        }
+    }
+    return 0;
+}
+
 /* Exercise decision of the rule at date k for n given points (tests replay decisions). */
 int orc_exercise(const orc_model *M, const orc_rule *R, int k, int n, const double *S, int *out)
 {

@@ -818,6 +818,7 @@ bap_status validate_cmc(const bap_option* o, const bap_cmc_params* p) {
     if (p->J < 2 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 2..8192", p->J);
     if (p->N2 < 1 || p->N2 > (1LL << 31)) return fail(BAP_EINVAL, "N2 outside 1..2^31");
     if (p->n_stumps < 1 || p->n_stumps > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "n_stumps outside 1..%d", BAP_MAX_STUMPS);
+    if (p->sampler != 0 && p->sampler != 1) return fail(BAP_EINVAL, "sampler outside 0..1");
     return BAP_OK;
 }
 
@@ -970,6 +971,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     TRY(o->sorted_v.reserve((size_t)nF * J * 8));
     TRY(o->sorted_i.reserve((size_t)nF * J * 4));
     TRY(o->err.reserve((size_t)nF * J * 8));
+    if (p->sampler == 1) TRY(o->bridge_w.reserve((size_t)J * d * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
     TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
     TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
@@ -996,7 +998,8 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     for (int m = o->n_dates - 1; m >= 1; --m) {
         train_points_kernel<<<(J + 127) / 128, 128, 0, st>>>(
             o->dmodel.as<DevModel>(), m, make_round_keys(p->seed, P_TRAIN, (uint32_t)m), J,
-            o->start.as<double>(), o->ctr_item.as<int>());
+            o->start.as<double>(), o->ctr_item.as<int>(),
+            p->sampler == 1 ? o->bridge_w.as<double>() : nullptr, m < o->n_dates - 1 ? 1 : 0);
         ++o->launches;
         CU(cudaGetLastError());
         CU(cudaMemsetAsync(o->work.p, 0, 8, st));
@@ -1123,7 +1126,7 @@ size_t estimate_bytes(const bap_model* md, int method, const void* params, int64
         const bap_cmc_params* p = static_cast<const bap_cmc_params*>(params);
         n = (size_t)p->J;
         C = (size_t)((p->N2 + choose_chunk((long long)n, p->N2) - 1) / choose_chunk((long long)n, p->N2));
-        extra = (d + 1) * n * 20;
+        extra = (d + 1) * n * 20 + d * n * 8;     // sorted features, bridge state
         rules = nd * (size_t)p->n_stumps * 64;
     }
     const size_t items = n * (d * 8 + sizeof(ItemState) + 40) + n * C * 32 + nd * n * 16;

@@ -344,7 +344,7 @@ __global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int de
 // draws from the law of S_{t_m}).
 
 __global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int J, double* start,
-                                    int* ctr_item) {
+                                    int* ctr_item, double* W, int bridge_from_next) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= J) return;
     const int d = M->d;
@@ -360,11 +360,31 @@ __global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int 
         z[4 * c + 3] = a1;
     }
     const double tm = M->t[m];
-    for (int q = 0; q < d; ++q) {
-        double wq = 0.0;
-        for (int i = 0; i <= q; ++i) wq += M->L[q * MAXD + i] * z[i];
-        const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
-        start[(size_t)j * d + q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * wq);
+    if (W == nullptr) {
+        for (int q = 0; q < d; ++q) {
+            double wq = 0.0;
+            for (int i = 0; i <= q; ++i) wq += M->L[q * MAXD + i] * z[i];
+            const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+            start[(size_t)j * d + q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * wq);
+        }
+    } else {
+        // Brownian bridge (Section 3.3): W_m = a W_{m+1} + b L z with a = t_m / t_{m+1} and
+        // b = sqrt(t_m (t_{m+1} - t_m) / t_{m+1}); at the last fitted date a = 0, b = sqrt(t_m).
+        // W holds this point's W_{m+1} on entry and W_m on exit.
+        double a = 0.0, b = sqrt(tm);
+        if (bridge_from_next) {
+            const double tn = M->t[m + 1];
+            a = tm / tn;
+            b = sqrt(tm * (tn - tm) / tn);
+        }
+        for (int q = 0; q < d; ++q) {
+            double lz = 0.0;
+            for (int i = 0; i <= q; ++i) lz += M->L[q * MAXD + i] * z[i];
+            const double w = b * lz + (bridge_from_next ? a * W[(size_t)j * d + q] : 0.0);
+            const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+            W[(size_t)j * d + q] = w;
+            start[(size_t)j * d + q] = M->S0[q] * exp(mu * tm + M->sigma[q] * w);
+        }
     }
     ctr_item[j] = j;
 }

@@ -16,7 +16,7 @@ __global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int de
                               const double* start, const ItemState* state, double* coef64,
                               float* coef_f, double* coef_d, int* fitted);
 __global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int J, double* start,
-                                    int* ctr_item);
+                                    int* ctr_item, double* W, int bridge_from_next);
 __global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int* n_stumps,
                                  const int* feat, const double* thr, const int* pol,
                                  const double* alpha, int rec_len, float* rec_f, double* rec_d);

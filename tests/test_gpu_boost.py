@@ -88,3 +88,34 @@ def test_boost_form_argument_checks():
         opt.set_boost_form(2)
     assert e.value.status == bap.BAP_EINVAL
     opt.close()
+
+
+def test_bridged_training_points_match_the_oracle():
+    """CMC with the Brownian-bridge sampler: the GPU's per-date labels y = Phi - C at the bridged
+    points agree with the oracle's, and so do the prices."""
+    import numpy as np
+    spec = spec_basket_put_7(0)
+    params = CMCParams(J=400, N2=1000, n_stumps=40, seed=5, sampler=1)
+    opt = bap.Option(spec)
+    opt.fit_classifier(params)
+    o_rules, o_diag = oracle.cmc_fit(spec, params, n_threads=8)
+    agree = total = 0
+    for m, dg in o_diag.items():
+        y, _, _ = opt.fit_points(m)
+        agree += int(np.sum(np.sign(y) == np.sign(dg["y"])))
+        total += len(y)
+        close = np.abs(y - dg["y"]) <= 1e-4 * np.maximum(1.0, np.abs(dg["y"])) + 2e-4
+        assert close.mean() >= 0.97, m
+    assert agree >= total - 3
+    g = opt.price(200_000, 6)
+    o = oracle.price(spec, o_rules, 200_000, 6, n_threads=8)
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"], (g, o)
+    opt.close()
+
+
+def test_sampler_argument_checks():
+    opt = bap.Option(spec_put_1d(n_dates=3))
+    with pytest.raises(bap.BapError) as e:
+        opt.fit_classifier(CMCParams(J=16, N2=64, n_stumps=4, seed=1, sampler=2))
+    assert e.value.status == bap.BAP_EINVAL
+    opt.close()

@@ -66,3 +66,25 @@ def test_table4_cmc_against_binomial(s0):
     assert r["price"] > g["binomial"] * (1 - 0.006), (r["price"], g)
     # Table 4's variance column is the variance of the exercised payoff
     assert abs(r["var"] - g["variance"]) / g["variance"] < 0.05
+
+
+def test_fixed_point_iteration_against_newton():
+    """Section 2.4's literal fixed-point iteration (eps = 0.01) and the safeguarded Newton reach
+    the same price on the Table 1 workload; Newton needs far fewer continuation evaluations per
+    boundary point."""
+    import numpy as np
+    spec = spec_max_call(3, 90.0)
+    res = {}
+    for fp in (0, 1):
+        o = bap.Option(spec)
+        o.fit_boundary(IZParams(J=128, N1=5000, degree=2, seed=1, fixed_point=fp, fp_eps=0.01,
+                                max_iter=100))
+        r = o.price(N, 2)
+        its = np.concatenate([o.fit_points(m)[1] for m in range(1, spec.n_dates)])
+        o.close()
+        res[fp] = (r, its)
+    (rn, itn), (rf, itf) = res[0], res[1]
+    assert rn["n_noconv"] == 0
+    assert abs(rn["price"] - rf["price"]) < 3 * np.hypot(rn["se"], rf["se"])
+    assert itf.mean() > 1.5 * itn.mean()
+    assert rf["fit_path_steps"] > rn["fit_path_steps"]
