@@ -431,7 +431,7 @@ bap_status enqueue_iz_setup(bap_option* o, const bap_iz_params* p, int m, bool d
 }
 
 bap_status enqueue_iz_fit_date_end(bap_option* o, const bap_iz_params* p, int m) {
-    ls_fit_kernel<<<o->n_bnd, 256, 0, o->stream>>>(
+    ls_fit_kernel<<<o->n_bnd, kLsThreads, 0, o->stream>>>(
         o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->degree, o->n_coef, o->start.as<double>(),
         o->state.as<ItemState>(), o->coef64.as<double>(), o->coef_f.as<float>(),
         o->coef_d.as<double>(), o->fitted.as<int>());

@@ -201,7 +201,7 @@ __device__ inline double basis_val(const double* y, int bi, int bj) {
     return a * b;
 }
 
-__global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
+__global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
                               const double* start, const ItemState* state, double* coef64,
                               float* coef_f, double* coef_d, int* fitted) {
     const int b = blockIdx.x;
@@ -251,32 +251,72 @@ __global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int de
     const double mean = n_used > 0 ? red[0] / n_used : 0.0;
     bool use_mean = n_used < P;
     if (!use_mean) {
+        // Normal equations: entry (r, c) of G (and r of the right side, column P below) is the
+        // sum over the used points, in point order, of basis_r * basis_c.  The basis values of
+        // kChunk points at a time are staged in shared memory once; each thread keeps the sums
+        // of its own entries e = threadIdx.x + k * blockDim.x.
         const int npair = P * (P + 1) / 2;
-        for (int e = threadIdx.x; e < npair + P; e += blockDim.x) {
-            int r = 0, c = 0;
+        constexpr int kChunk = 32;
+        constexpr int kEPT = (MAXCOEF * (MAXCOEF + 1) / 2 + MAXCOEF + kLsThreads - 1) / kLsThreads;
+        __shared__ double Bs[kChunk][MAXCOEF + 1];
+        __shared__ int Bu[kChunk];
+        int er[kEPT], ec[kEPT];
+        double acc[kEPT];
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int e = threadIdx.x + k * kLsThreads;
+            int r = -1, c = -1;
             if (e < npair) {
                 int rem = e;
+                r = 0;
                 while (rem >= P - r) { rem -= P - r; ++r; }
                 c = r + rem;
-            } else {
+            } else if (e < npair + P) {
                 r = e - npair;
-                c = -1;
+                c = P;
             }
-            double acc = 0.0;
-            for (int j = 0; j < J; ++j) {
-                const int item = b * J + j;
-                if (state[item].status == ST_NOROOT) continue;
-                const double* S = start + (size_t)item * d;
-                double y[MAXD];
-                int t = 0;
-                for (int q = 0; q < d; ++q)
-                    if (q != p) y[t++] = S[q] / K;
-                const double fr = basis_val(y, bi[r], bj[r]);
-                const double fc = c >= 0 ? basis_val(y, bi[c], bj[c]) : state[item].x / K;
-                acc += fr * fc;
+            er[k] = r;
+            ec[k] = c;
+            acc[k] = 0.0;
+        }
+        for (int j0 = 0; j0 < J; j0 += kChunk) {
+            for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+                const int j = j0 + t;
+                int used = 0;
+                if (j < J) {
+                    const int item = b * J + j;
+                    if (state[item].status != ST_NOROOT) {
+                        used = 1;
+                        const double* S = start + (size_t)item * d;
+                        double y[MAXD];
+                        int u = 0;
+                        for (int q = 0; q < d; ++q)
+                            if (q != p) y[u++] = S[q] / K;
+                        for (int r = 0; r < P; ++r) Bs[t][r] = basis_val(y, bi[r], bj[r]);
+                        Bs[t][P] = state[item].x / K;
+                    }
+                }
+                Bu[t] = used;
             }
-            if (c >= 0) { G[r * P + c] = acc; G[c * P + r] = acc; }
-            else rhs[r] = acc;
+            __syncthreads();
+            // a thread's entries are a prefix of its slots: stop at the first empty one, so that
+            // warps without entries issue no FP64 work (the FP64 pipe is 1/64 of the FP32 rate)
+            for (int t = 0; t < kChunk; ++t) {
+                if (!Bu[t]) continue;
+#pragma unroll
+                for (int k = 0; k < kEPT; ++k) {
+                    if (er[k] < 0) break;
+                    acc[k] += Bs[t][er[k]] * Bs[t][ec[k]];
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < kEPT; ++k) {
+            const int r = er[k], c = ec[k];
+            if (r < 0) continue;
+            if (c < P) { G[r * P + c] = acc[k]; G[c * P + r] = acc[k]; }
+            else rhs[r] = acc[k];
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -12,6 +12,8 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
                                 int* count);
 __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
                                 int degree, double K, float* coef_f, double* coef_d);
+// Threads per block of ls_fit_kernel (one block per boundary).
+constexpr int kLsThreads = 256;
 __global__ void ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
                               const double* start, const ItemState* state, double* coef64,
                               float* coef_f, double* coef_d, int* fitted);
