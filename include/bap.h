@@ -165,6 +165,13 @@ bap_status bap_set_profiling(bap_option *opt, int on);
  * ECUDA.  All three forms give bitwise the same fit.  Errors: EINVAL (mode outside 0..2). */
 bap_status bap_set_launch_mode(bap_option *opt, int mode);
 
+/* Upper bound, in ns, of one wait at a grid barrier of the cooperative Newton launch (launch
+ * form 2).  A block that waits longer gives up, the launch ends, and the fit returns ECUDA with
+ * the reason; the option and the device stay usable.  0 (default): 5 s plus 1 ns per inner
+ * path-step of the date, far above any real pass.  Small values serve to test that path.
+ * Errors: EINVAL (null option). */
+bap_status bap_set_wait_limit(bap_option *opt, uint64_t ns);
+
 /* How bap_fit_classifier runs the boosting of each date ([class], Section 3.2; the paper's
  * sequential bottleneck).  1 (default): a thread-block cluster of d+1 blocks, one per feature,
  * each sorting and scanning its feature while the blocks exchange per-round minima through

@@ -23,7 +23,7 @@ PURPOSE_IZ, PURPOSE_CMC, PURPOSE_TRAIN, PURPOSE_PRICE = 1, 2, 3, 4
 MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
 EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
-            "bap_set_boost_form", "bap_last_boost_form",
+            "bap_set_boost_form", "bap_last_boost_form", "bap_set_wait_limit",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
             "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
@@ -96,6 +96,7 @@ def lib():
         L.bap_set_profiling.argtypes = [vp, C.c_int]
         L.bap_set_launch_mode.argtypes = [vp, C.c_int]
         L.bap_set_boost_form.argtypes = [vp, C.c_int]
+        L.bap_set_wait_limit.argtypes = [vp, C.c_uint64]
         L.bap_last_boost_form.argtypes = [vp, C.POINTER(C.c_int)]
         L.bap_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
         L.bap_server_set_launch_mode.argtypes = [vp, C.c_int]
@@ -198,6 +199,9 @@ class Option:
 
     def set_launch_mode(self, mode: int):
         _check(lib().bap_set_launch_mode(self.h, mode))
+
+    def set_wait_limit(self, ns: int):
+        _check(lib().bap_set_wait_limit(self.h, ns))
 
     def set_boost_form(self, form: int):
         _check(lib().bap_set_boost_form(self.h, form))

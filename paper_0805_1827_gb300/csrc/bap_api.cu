@@ -377,8 +377,10 @@ bap_status enqueue_newton_coop(bap_option* o, const bap_iz_params* p, int m, int
     a.coop_bar = reinterpret_cast<unsigned*>(o->counts.as<int>() + p->max_iter + 1);
     a.coop_err = o->stat_counts.as<int>() + 3;
     // a wait at the barrier never lasts longer than a pass: allow 5 s plus 1 ns per path step
-    a.coop_limit_ns = 5000000000ULL + (unsigned long long)o->n_items *
-                                          (unsigned long long)p->N1 * (unsigned long long)(o->n_dates - m);
+    a.coop_limit_ns = o->wait_limit_ns != 0
+                          ? o->wait_limit_ns
+                          : 5000000000ULL + (unsigned long long)o->n_items *
+                                                (unsigned long long)p->N1 * (unsigned long long)(o->n_dates - m);
     a.start = o->start.as<double>();
     a.ctr_item = o->ctr_item.as<int>();
     a.pivot = o->pivot.as<int>();
@@ -1168,6 +1170,12 @@ bap_status bap_set_launch_mode(bap_option* o, int mode) {
     if (mode != LAUNCH_PLAIN && mode != LAUNCH_GRAPH && mode != LAUNCH_COOP)
         return fail(BAP_EINVAL, "bad launch mode");
     o->launch_mode = mode;
+    return BAP_OK;
+}
+
+bap_status bap_set_wait_limit(bap_option* o, uint64_t ns) {
+    if (!o) return fail(BAP_EINVAL, "null option");
+    o->wait_limit_ns = ns;
     return BAP_OK;
 }
 

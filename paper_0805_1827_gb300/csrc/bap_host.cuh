@@ -139,6 +139,7 @@ struct bap_option {
     // graph of the I&Z fit (Newton loops as conditional while nodes)
     int launch_mode = bap::LAUNCH_GRAPH;
     int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device
+    unsigned long long wait_limit_ns = 0;   // grid-barrier wait bound; 0: automatic
     int boost_form = 1;           // CMC boosting: 1 cluster of d+1 blocks, 0 one block
     int last_boost_cluster = 0;   // form the last CMC fit ran
     cudaGraphExec_t graph_exec = nullptr;
