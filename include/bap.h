@@ -44,7 +44,8 @@ typedef enum {
     BAP_ENOTREADY = 5,  /* bap_poll: the request is not finished yet */
     BAP_EBUSY = 6,      /* bap_submit: admission refused (memory budget or slots full) */
     BAP_ETIMEOUT = 7,   /* a bounded device wait gave up */
-    BAP_ESTATE = 8      /* call out of order, e.g. bap_price before a fit */
+    BAP_ESTATE = 8,     /* call out of order, e.g. bap_price before a fit */
+    BAP_ECANCELED = 9   /* served request cancelled by bap_cancel */
 } bap_status;
 
 /* Payoff Phi(S) at an exercise date (Section 2.2 defines the max-call). */
@@ -126,6 +127,12 @@ typedef struct bap_result {
                                  bap_price is not timed */
     double queue_ms;          /* served requests: submit -> admission (host clock) */
     double latency_ms;        /* served requests: submit -> completion (host clock) */
+    double phase_ms[4];       /* device time per phase of the paper's time distributions (CUDA
+                                 events; the fit's phases only with bap_set_profiling on and a
+                                 non-graph launch form, else 0): I&Z [0] [glp] lattice and point
+                                 set-up, [1] [calc] Newton passes, [2] [reg] least squares;
+                                 CMC [0] 0, [1] [calc] training points and labels, [2] [class]
+                                 boosting; both [3] [mc] pricing (= price_ms) */
 } bap_result;
 
 typedef struct bap_server_stats {
@@ -138,6 +145,7 @@ typedef struct bap_server_stats {
     double fit_enqueue_ms;    /*   enqueueing fits (for I&Z including building the graph) */
     double price_enqueue_ms;  /*   enqueueing pricing */
     double finish_ms;         /* server-thread host time spent finishing requests */
+    int64_t cancelled;        /* requests ended by bap_cancel (also counted in failed) */
 } bap_server_stats;
 
 typedef struct bap_option bap_option;
@@ -282,6 +290,14 @@ bap_status bap_submit(bap_server *srv, const bap_model *model, int method, const
  * (OK, ENOCONV, or its error) with *out filled (may be NULL), after which the ticket is gone.
  * EINVAL for an unknown ticket. */
 bap_status bap_poll(bap_server *srv, uint64_t ticket, bap_result *out);
+
+/* Cancel a request that has not been collected.  Queued: it is dropped at once.  Running: the
+ * server sets the request's device abort flag (the one the cooperative Newton launch checks at
+ * every grid barrier, so an I&Z fit in launch form 2 stops at its next pass) and discards the
+ * result when the request's work ends.  Either way bap_poll / bap_wait then return ECANCELED.
+ * A request already finished keeps its result (returns ESTATE).  Thread safe.
+ * Errors: EINVAL (null server, unknown ticket), ESTATE (already finished). */
+bap_status bap_cancel(bap_server *srv, uint64_t ticket);
 
 /* As bap_poll, but waits up to timeout_s seconds; BAP_ETIMEOUT if still not done. */
 bap_status bap_wait(bap_server *srv, uint64_t ticket, double timeout_s, bap_result *out);

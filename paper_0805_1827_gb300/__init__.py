@@ -15,9 +15,9 @@ import numpy as np
 from ._build import LIB as _LIB_PATH, build, needs_build   # noqa: F401
 
 BAP_OK, BAP_EINVAL, BAP_ENOMEM, BAP_ECUDA, BAP_ENOCONV = 0, 1, 2, 3, 4
-BAP_ENOTREADY, BAP_EBUSY, BAP_ETIMEOUT, BAP_ESTATE = 5, 6, 7, 8
+BAP_ENOTREADY, BAP_EBUSY, BAP_ETIMEOUT, BAP_ESTATE, BAP_ECANCELED = 5, 6, 7, 8, 9
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENOTREADY",
-                6: "EBUSY", 7: "ETIMEOUT", 8: "ESTATE"}
+                6: "EBUSY", 7: "ETIMEOUT", 8: "ESTATE", 9: "ECANCELED"}
 PAYOFF_CODE = {"max_call": 0, "basket_put": 1, "geo_call": 2}
 PURPOSE_IZ, PURPOSE_CMC, PURPOSE_TRAIN, PURPOSE_PRICE = 1, 2, 3, 4
 MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
@@ -27,7 +27,7 @@ EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
             "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
-            "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait",
+            "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait", "bap_cancel",
             "bap_server_get_stats", "bap_server_destroy"]
 LAUNCH_PLAIN, LAUNCH_GRAPH, LAUNCH_COOP = 0, 1, 2
 BOOST_ONE_BLOCK, BOOST_CLUSTER = 0, 1
@@ -66,7 +66,15 @@ class _Result(C.Structure):
                 ("fit_path_steps", C.c_int64), ("fit_ms", C.c_double), ("price_ms", C.c_double),
                 ("kernel_launches", C.c_int64), ("path_launches", C.c_int64),
                 ("path_kernel_ms", C.c_double), ("queue_ms", C.c_double),
-                ("latency_ms", C.c_double)]
+                ("latency_ms", C.c_double), ("phase_ms", C.c_double * 4)]
+
+
+def _res_dict(r) -> dict:
+    out = {}
+    for k, _ in _Result._fields_:
+        v = getattr(r, k)
+        out[k] = list(v) if k == "phase_ms" else v
+    return out
 
 
 class _ServerStats(C.Structure):
@@ -74,7 +82,7 @@ class _ServerStats(C.Structure):
                 ("queued", C.c_int64), ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64),
                 ("peak_inflight", C.c_int64), ("start_ms", C.c_double), ("load_ms", C.c_double),
                 ("fit_enqueue_ms", C.c_double), ("price_enqueue_ms", C.c_double),
-                ("finish_ms", C.c_double)]
+                ("finish_ms", C.c_double), ("cancelled", C.c_int64)]
 
 
 _lib = None
@@ -105,6 +113,7 @@ def lib():
         L.bap_poll.argtypes = [vp, C.c_uint64, C.POINTER(_Result)]
         L.bap_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(_Result)]
         L.bap_server_get_stats.argtypes = [vp, C.POINTER(_ServerStats)]
+        L.bap_cancel.argtypes = [vp, C.c_uint64]
         L.bap_server_destroy.argtypes = [vp]
         L.bap_server_destroy.restype = None
         L.bap_fit_boundary.argtypes = [vp, C.POINTER(_IZ)]
@@ -222,7 +231,7 @@ class Option:
     def price(self, n_paths: int, seed: int) -> dict:
         r = _Result()
         _check(lib().bap_price(self.h, n_paths, seed, C.byref(r)))
-        return {k: getattr(r, k) for k, _ in _Result._fields_}
+        return _res_dict(r)
 
     def export_rules(self) -> np.ndarray:
         n = C.c_size_t(0)
@@ -292,13 +301,16 @@ class Server:
         if st == BAP_ENOTREADY:
             return None
         _check(st, (BAP_OK, BAP_ENOCONV))
-        return st, {k: getattr(r, k) for k, _ in _Result._fields_}
+        return st, _res_dict(r)
+
+    def cancel(self, ticket: int):
+        _check(lib().bap_cancel(self.h, ticket))
 
     def wait(self, ticket: int, timeout_s: float = 600.0):
         r = _Result()
         st = lib().bap_wait(self.h, ticket, timeout_s, C.byref(r))
         _check(st, (BAP_OK, BAP_ENOCONV))
-        return st, {k: getattr(r, k) for k, _ in _Result._fields_}
+        return st, _res_dict(r)
 
     def stats(self) -> dict:
         s = _ServerStats()

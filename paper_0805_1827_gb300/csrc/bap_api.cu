@@ -12,6 +12,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bap_host.cuh"
 
 using namespace bap;
@@ -206,6 +208,46 @@ double prof_collect(bap_option* o) {
     }
     o->prof_used = 0;
     return tot;
+}
+
+// Phases of a fit, named as in the paper's time distributions: [glp] lattice and point set-up,
+// [calc] continuation values (Newton passes, CMC labels), [reg] / [class] the boundary fit or
+// the boosting.  Each phase is an NVTX range on the enqueuing host thread and, with profiling
+// on (and not inside a graph capture), a pair of CUDA events on the option's stream.
+enum Phase : int { PH_GLP = 0, PH_CALC = 1, PH_FIT = 2 };
+const char* const kPhaseName[3] = {"[glp]", "[calc]", "[reg/class]"};
+
+int phase_begin(bap_option* o, int phase) {
+    nvtxRangePushA(kPhaseName[phase]);
+    if (!o->profiling || o->capturing) return -1;
+    if (o->phase_ev.size() <= o->phase_used) {
+        bap_option::PhaseMark pm{phase, nullptr, nullptr};
+        if (cudaEventCreate(&pm.a) != cudaSuccess || cudaEventCreate(&pm.b) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        o->phase_ev.push_back(pm);
+    }
+    const int i = (int)o->phase_used++;
+    o->phase_ev[i].phase = phase;
+    cudaEventRecord(o->phase_ev[i].a, o->stream);
+    return i;
+}
+
+void phase_end(bap_option* o, int i) {
+    nvtxRangePop();
+    if (i >= 0) cudaEventRecord(o->phase_ev[i].b, o->stream);
+}
+
+// Sums the recorded phases of the last fit (after the stream reached them).
+void phase_collect(bap_option* o) {
+    for (double& v : o->fit_phase_ms) v = 0.0;
+    for (size_t i = 0; i < o->phase_used; ++i) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, o->phase_ev[i].a, o->phase_ev[i].b) == cudaSuccess)
+            o->fit_phase_ms[o->phase_ev[i].phase] += ms;
+    }
+    o->phase_used = 0;
 }
 
 void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
@@ -834,6 +876,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
     o->prof_used = 0;
+    o->phase_used = 0;
     TRY(set_rule_iz(o, p->degree));
     o->method = 0;
     if (o->n_dates < 2) {
@@ -879,14 +922,28 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
         // the device and added by finish_fit_iz
         o->launches += 2 + (p->J > 2 && o->d >= 3) + 3LL * (o->n_dates - 1);
     } else {
-        TRY(enqueue_iz_prologue(o, p));
+        int ph = phase_begin(o, PH_GLP);
+        bap_status st = enqueue_iz_prologue(o, p);
+        phase_end(o, ph);
+        TRY(st);
         for (int m = o->n_dates - 1; m >= 1; --m) {
-            TRY(enqueue_iz_setup(o, p, m, false));
-            if (o->launch_mode == LAUNCH_COOP)
-                TRY(enqueue_newton_coop(o, p, m, chunk, C));
-            else
-                for (int it = 0; it < p->max_iter; ++it) TRY(enqueue_newton_pass(o, p, m, it, chunk, C));
-            TRY(enqueue_iz_fit_date_end(o, p, m));
+            ph = phase_begin(o, PH_GLP);
+            st = enqueue_iz_setup(o, p, m, false);
+            phase_end(o, ph);
+            TRY(st);
+            ph = phase_begin(o, PH_CALC);
+            if (o->launch_mode == LAUNCH_COOP) {
+                st = enqueue_newton_coop(o, p, m, chunk, C);
+            } else {
+                for (int it = 0; it < p->max_iter && st == BAP_OK; ++it)
+                    st = enqueue_newton_pass(o, p, m, it, chunk, C);
+            }
+            phase_end(o, ph);
+            TRY(st);
+            ph = phase_begin(o, PH_FIT);
+            st = enqueue_iz_fit_date_end(o, p, m);
+            phase_end(o, ph);
+            TRY(st);
         }
     }
     CU(cudaEventRecord(o->ev1, st));
@@ -911,6 +968,7 @@ bap_status finish_fit_iz(bap_option* o) {
     o->fit_launches = o->launches;
     o->fit_path_launches = o->path_launches;
     o->fit_path_ms = prof_collect(o);
+    phase_collect(o);
     return o->last_noconv > 0 ? BAP_ENOCONV : BAP_OK;
 }
 
@@ -953,6 +1011,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
     o->prof_used = 0;
+    o->phase_used = 0;
     TRY(set_rule_cmc(o, p->n_stumps));
     o->method = 1;
     cudaStream_t st = o->stream;
@@ -998,6 +1057,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     }
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
+        const int ph_calc = phase_begin(o, PH_CALC);
         train_points_kernel<<<(J + 127) / 128, 128, 0, st>>>(
             o->dmodel.as<DevModel>(), m, make_round_keys(p->seed, P_TRAIN, (uint32_t)m), J,
             o->start.as<double>(), o->ctr_item.as<int>(),
@@ -1023,7 +1083,10 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         a.done = o->done.as<int>();
         a.label_y = o->label_y.as<double>();
         a.label = o->label.as<int>();
-        TRY(launch_path(o, a, R_CMC, false, (long long)n * C));
+        const bap_status sl = launch_path(o, a, R_CMC, false, (long long)n * C);
+        phase_end(o, ph_calc);
+        TRY(sl);
+        const int ph_fit = phase_begin(o, PH_FIT);
         if (cluster) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -1044,8 +1107,11 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
                 o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
         }
         ++o->launches;
-        CU(cudaGetLastError());
-        TRY(record_diag(o, m, false));
+        const cudaError_t eb = cudaGetLastError();
+        const bap_status sd = eb == cudaSuccess ? record_diag(o, m, false) : BAP_OK;
+        phase_end(o, ph_fit);
+        if (eb != cudaSuccess) return fail(BAP_ECUDA, "boosting launch: %s", cudaGetErrorString(eb));
+        TRY(sd);
     }
     CU(cudaEventRecord(o->ev1, st));
     CU(cudaMemcpyAsync(&o->pin->fit_steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
@@ -1061,6 +1127,7 @@ bap_status finish_fit_cmc(bap_option* o) {
     o->fit_launches = o->launches;
     o->fit_path_launches = o->path_launches;
     o->fit_path_ms = prof_collect(o);
+    phase_collect(o);
     return BAP_OK;
 }
 
@@ -1111,6 +1178,8 @@ bap_status finish_price(bap_option* o, bap_result* res) {
     res->kernel_launches = o->fit_launches + o->launches;
     res->path_launches = o->fit_path_launches + o->path_launches;
     res->path_kernel_ms = o->fit_path_ms + prof_collect(o);
+    for (int i = 0; i < 3; ++i) res->phase_ms[i] = o->fit_phase_ms[i];
+    res->phase_ms[3] = ms;
     return BAP_OK;
 }
 

@@ -136,6 +136,11 @@ struct bap_option {
     int capturing = 0;
     std::vector<cudaEvent_t> prof_ev;
     size_t prof_used = 0;
+    // per-phase device time of the last fit (profiling on): [0] glp, [1] calc, [2] reg / class
+    struct PhaseMark { int phase; cudaEvent_t a, b; };
+    std::vector<PhaseMark> phase_ev;
+    size_t phase_used = 0;
+    double fit_phase_ms[3] = {0, 0, 0};
     // graph of the I&Z fit (Newton loops as conditional while nodes)
     int launch_mode = bap::LAUNCH_GRAPH;
     int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device

@@ -40,6 +40,7 @@ struct Request {
     bap_option* opt = nullptr;
     cudaEvent_t done_ev = nullptr;
     int state = Q_QUEUED;
+    bool cancel = false;           // bap_cancel on a running request
     bap_status status = BAP_OK;
     std::string err;
     bap_result res{};
@@ -61,6 +62,7 @@ struct bap_server {
     int launch_mode = LAUNCH_COOP;
     bool stop = false;
     uint64_t next_ticket = 1;
+    cudaStream_t cancel_stream = nullptr;          // writes device abort flags (server thread)
     bap_server_stats stats{};
     std::thread th;
 };
@@ -128,6 +130,10 @@ void release(bap_server* s, Request* r) {
 
 void server_loop(bap_server* s) {
     cudaSetDevice(s->device);
+    if (cudaStreamCreateWithFlags(&s->cancel_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s->cancel_stream = nullptr;
+    }
     for (;;) {
         std::vector<Request*> admit;
         {
@@ -170,11 +176,30 @@ void server_loop(bap_server* s) {
             Request* r = s->running[i];
             const cudaError_t q = cudaEventQuery(r->done_ev);
             if (q == cudaErrorNotReady) {
+                bool cancel;
+                {
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    cancel = r->cancel;
+                }
+                // a cancelled request: keep its abort flag set (the fit's set-up clears it once)
+                if (cancel && s->cancel_stream)
+                    cudaMemsetAsync(r->opt->stat_counts.as<int>() + 3, 0x01, sizeof(int), s->cancel_stream);
                 ++i;
                 continue;
             }
             const auto t0 = Clock::now();
-            if (q == cudaSuccess) {
+            bool cancelled;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                cancelled = r->cancel;
+            }
+            if (cancelled) {
+                if (q != cudaSuccess) cudaGetLastError();
+                // no abort-flag write may land after this slot goes to the next request
+                if (s->cancel_stream) cudaStreamSynchronize(s->cancel_stream);
+                r->status = BAP_ECANCELED;
+                r->err = "cancelled";
+            } else if (q == cudaSuccess) {
                 finish_request(r);
             } else {
                 r->status = BAP_ECUDA;
@@ -189,6 +214,7 @@ void server_loop(bap_server* s) {
                 r->t_done = Clock::now();
                 if (r->status == BAP_OK || r->status == BAP_ENOCONV) s->stats.completed += 1;
                 else s->stats.failed += 1;
+                if (r->status == BAP_ECANCELED) s->stats.cancelled += 1;
                 s->cv_done.notify_all();
             }
             s->running[i] = s->running.back();
@@ -203,6 +229,10 @@ void server_loop(bap_server* s) {
     }
     for (bap_option* o : s->free_slots) option_destroy(o);
     s->free_slots.clear();
+    if (s->cancel_stream) {
+        cudaStreamSynchronize(s->cancel_stream);
+        cudaStreamDestroy(s->cancel_stream);
+    }
 }
 
 }  // namespace
@@ -319,6 +349,30 @@ bap_status bap_poll(bap_server* s, uint64_t ticket, bap_result* out) {
     if (it == s->table.end()) return fail(BAP_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
     if (it->second->state != Q_DONE) return BAP_ENOTREADY;
     return collect(s, it, out);
+}
+
+bap_status bap_cancel(bap_server* s, uint64_t ticket) {
+    clear_error();
+    if (!s) return fail(BAP_EINVAL, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return fail(BAP_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Request* r = it->second;
+    if (r->state == Q_DONE) return fail(BAP_ESTATE, "request %llu already finished", (unsigned long long)ticket);
+    if (r->state == Q_QUEUED) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == r) { s->queue.erase(q); break; }
+        r->state = Q_DONE;
+        r->status = BAP_ECANCELED;
+        r->err = "cancelled";
+        r->t_admit = r->t_done = Clock::now();
+        s->stats.failed += 1;
+        s->stats.cancelled += 1;
+        s->cv_done.notify_all();
+    } else {
+        r->cancel = true;
+    }
+    return BAP_OK;
 }
 
 bap_status bap_wait(bap_server* s, uint64_t ticket, double timeout_s, bap_result* out) {

@@ -116,3 +116,58 @@ def test_server_cmc_and_mixed_memory_pressure():
         assert res["price"] == _alone(req)["price"]
     assert srv.stats()["peak_bytes"] <= 64 << 20 or srv.stats()["peak_inflight"] == 1
     srv.close()
+
+
+def test_cancel_queued_and_running_requests():
+    """A queued request is dropped at once; a running I&Z request (cooperative launch form) has
+    its abort flag set and ends early; both report ECANCELED; the server keeps serving and the
+    next result equals the same request run alone."""
+    spec = spec_max_call(5, 100.0, rho=0.3, n_dates=9, T=3.0)
+    big = IZParams(J=512, N1=100_000, degree=2, seed=1)
+    srv = bap.Server(device_mem_budget=8 << 30, max_inflight=1)
+    t_run = srv.submit(spec, big, 100_000, 1)
+    t_queued = srv.submit(spec, big, 100_000, 2)
+    small = IZParams(J=16, N1=2000, degree=1, seed=3)
+    t_after = srv.submit(spec_put_1d(n_dates=5), small, 20_000, 4)
+    srv.cancel(t_queued)
+    import time
+    time.sleep(0.05)                      # let the first request start
+    srv.cancel(t_run)
+    for t in (t_queued, t_run):
+        with pytest.raises(bap.BapError) as e:
+            srv.wait(t, 120.0)
+        assert e.value.status == bap.BAP_ECANCELED
+    st, res = srv.wait(t_after, 120.0)
+    assert st in (bap.BAP_OK, bap.BAP_ENOCONV)
+    alone = bap.Option(spec_put_1d(n_dates=5))
+    alone.set_launch_mode(bap.LAUNCH_COOP)
+    alone.fit_boundary(small)
+    ra = alone.price(20_000, 4)
+    alone.close()
+    assert res["price"] == ra["price"]
+    stats = srv.stats()
+    assert stats["cancelled"] == 2
+    with pytest.raises(bap.BapError) as e:
+        srv.cancel(999_999)
+    assert e.value.status == bap.BAP_EINVAL
+    srv.close()
+
+
+def test_phase_timers_cover_the_fit():
+    """With profiling on, the fit's device time splits into the paper's phases."""
+    o = bap.Option(spec_max_call(3, 100.0, rho=0.2, n_dates=6, T=2.0))
+    o.set_profiling(True)
+    o.set_launch_mode(bap.LAUNCH_COOP)
+    o.fit_boundary(IZParams(J=64, N1=20_000, degree=2, seed=3))
+    r = o.price(100_000, 5)
+    glp, calc, reg, mc = r["phase_ms"]
+    assert glp > 0 and calc > 0 and reg > 0 and mc > 0
+    assert calc > reg and calc > glp
+    assert abs((glp + calc + reg) - r["fit_ms"]) < 0.2 * r["fit_ms"] + 0.5
+    assert mc == r["price_ms"]
+    o.set_boost_form(bap.BOOST_CLUSTER)
+    o.fit_classifier(CMCParams(J=200, N2=500, n_stumps=20, seed=2))
+    r = o.price(50_000, 5)
+    glp, calc, cls, mc = r["phase_ms"]
+    assert glp == 0 and calc > 0 and cls > 0
+    o.close()
