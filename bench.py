@@ -409,6 +409,20 @@ def root_find_study(bap) -> dict:
     return out
 
 
+def boundary_degree_study(bap) -> dict:
+    """The I&Z boundary as a linear, quadratic or cubic polynomial (Section 2.2) on the Table 1
+    workload (3-asset max-call, J=128, N1=5e3, N=1e6): price, SE and fit time per degree."""
+    out = {}
+    for s0 in (90, 100, 110):
+        for deg in (1, 2, 3):
+            o = bap.Option(spec_max_call(3, float(s0)))
+            o.fit_boundary(IZParams(J=128, N1=5000, degree=deg, seed=1))
+            r = o.price(1_000_000, 2)
+            o.close()
+            out[f"S0={s0},degree={deg}"] = {"price": r["price"], "se": r["se"], "fit_ms": r["fit_ms"]}
+    return out
+
+
 def run_ours(args) -> None:
     import torch
     import paper_0805_1827_gb300 as bap
@@ -510,6 +524,7 @@ def run_ours(args) -> None:
     boost = cmc_boost_forms(bap, stream) if args.launch_forms else None
     tables = paper_tables(bap) if args.paper_tables else None
     rootfind = root_find_study(bap) if args.paper_tables else None
+    degrees = boundary_degree_study(bap) if args.paper_tables else None
 
     ops = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
@@ -544,6 +559,7 @@ def run_ours(args) -> None:
         "cmc_boost_forms": boost,
         "paper_tables": tables,
         "root_find_study": rootfind,
+        "boundary_degree_study": degrees,
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},

@@ -393,24 +393,51 @@ def n_basis(s: int, degree: int) -> int:
         n += s
     if degree >= 2:
         n += s * (s + 1) // 2
+    if degree >= 3:
+        n += s * (s + 1) * (s + 2) // 6
     return n
 
 
 def basis_matrix(Y: np.ndarray, degree: int) -> np.ndarray:
-    """Rows [1, y_a, y_a y_b (a <= b)] of the scaled other-asset values."""
+    """Rows [1, y_a, y_a y_b (a <= b), y_a y_b y_c (a <= b <= c)] of the scaled other-asset
+    values, up to the given degree (Section 2.2: quadratic or cubic)."""
     J, s = Y.shape
     cols = [np.ones(J)]
     if degree >= 1:
         cols += [Y[:, a] for a in range(s)]
     if degree >= 2:
         cols += [Y[:, a] * Y[:, b] for a in range(s) for b in range(a, s)]
+    if degree >= 3:
+        cols += [Y[:, a] * Y[:, b] * Y[:, c] for a in range(s) for b in range(a, s)
+                 for c in range(b, s)]
     return np.stack(cols, axis=1)
+
+
+def rank_deficient(A: np.ndarray, tol: float = 1e-13) -> bool:
+    """The design's Gram matrix, scaled to a unit diagonal, meets a Cholesky pivot <= tol: its
+    columns are numerically dependent (e.g. a small Korobov point set)."""
+    G = A.T @ A
+    dg = np.diag(G)
+    if np.any(dg <= 0):
+        return True
+    s = 1.0 / np.sqrt(dg)
+    G = G * np.outer(s, s)
+    p = G.shape[0]
+    L = np.zeros_like(G)
+    for j in range(p):
+        v = G[j, j] - L[j, :j] @ L[j, :j]
+        if not v > tol:
+            return True
+        L[j, j] = np.sqrt(v)
+        L[j + 1:, j] = (G[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return False
 
 
 def ls_fit(Y: np.ndarray, x: np.ndarray, K: float, degree: int, use=None) -> np.ndarray:
     """Unweighted least squares of x/K on the polynomial basis of Y/K (numpy lstsq).  Points
-    with use == False are left out; with fewer points than coefficients the fit drops to
-    degree 0 (their mean), and with none the boundary is "never exercise" (returned as None)."""
+    with use == False are left out; with fewer points than coefficients, or a numerically
+    rank-deficient design (rank_deficient), the fit drops to degree 0 (their mean), and with no
+    point the boundary is "never exercise" (returned as None)."""
     s = Y.shape[1]
     p = n_basis(s, degree)
     if use is None:
@@ -418,11 +445,11 @@ def ls_fit(Y: np.ndarray, x: np.ndarray, K: float, degree: int, use=None) -> np.
     Yu, xu = Y[use] / K, x[use] / K
     if len(xu) == 0:
         return None
-    if len(xu) < p:
+    A = basis_matrix(Yu, degree) if len(xu) >= p else None
+    if A is None or rank_deficient(A):
         c = np.zeros(p)
         c[0] = xu.mean()
         return c
-    A = basis_matrix(Yu, degree)
     c, *_ = np.linalg.lstsq(A, xu, rcond=None)
     return c
 

@@ -53,6 +53,8 @@ typedef ORC_REAL real;
 #endif
 
 #define ORC_MAXD 16
+/* basis size of a cubic in ORC_MAXD - 1 variables: 1 + 15 + 120 + 680 */
+#define ORC_MAXBASIS 816
 
 enum { PAY_MAX_CALL = 0, PAY_BASKET_PUT = 1, PAY_GEO_CALL = 2 };
 enum { RULE_NONE = 0, RULE_IZ = 1, RULE_CMC = 2 };
@@ -202,7 +204,9 @@ static double payoff_dlog(const orc_model *M, const real *S, int p)
     return M->w[p] * (phi + M->K);   /* geometric: w_p * G */
 }
 
-/* Quadratic (or lower) polynomial basis in s variables, ordered [1, y_a, y_a*y_b (a<=b)]. */
+/* Polynomial basis of degree <= 3 in s variables, ordered
+ * [1, y_a, y_a*y_b (a<=b), y_a*y_b*y_c (a<=b<=c)] (Section 2.2: the boundary is regressed on
+ * a quadratic or cubic in the other assets). */
 static int basis(int s, int degree, const double *y, double *phi)
 {
     int n = 0;
@@ -211,6 +215,10 @@ static int basis(int s, int degree, const double *y, double *phi)
     if (degree >= 2)
         for (int a = 0; a < s; ++a)
             for (int b = a; b < s; ++b) phi[n++] = y[a] * y[b];
+    if (degree >= 3)
+        for (int a = 0; a < s; ++a)
+            for (int b = a; b < s; ++b)
+                for (int c = b; c < s; ++c) phi[n++] = y[a] * y[b] * y[c];
     return n;
 }
 
@@ -226,7 +234,7 @@ static int exercise(const orc_model *M, const orc_rule *R, int k, const real *S)
     int d = M->d;
     if (R->kind == RULE_IZ) {
         int p = rule_pivot(M, S);
-        double y[ORC_MAXD], ph[200];
+        double y[ORC_MAXD], ph[ORC_MAXBASIS];
         int s = 0;
         for (int q = 0; q < d; ++q) if (q != p) y[s++] = (double)S[q] / M->K;
         int nb = basis(s, R->degree, y, ph);

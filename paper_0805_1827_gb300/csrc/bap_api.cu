@@ -163,7 +163,17 @@ int choose_chunk(long long n_items, long long N) {
     return (int)c;
 }
 
+// The kernel for a rule: a cubic I&Z boundary has kernels of its own.
+int kernel_rule(const bap_option* o, int rule) {
+    if (o->rule_kind == R_IZ && o->degree >= 3) {
+        if (rule == R_IZ) return R_IZ3;
+        if (rule == R_NEWTON_COOP) return R_NEWTON_COOP3;
+    }
+    return rule;
+}
+
 bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units) {
+    rule = kernel_rule(o, rule);
     const void* fn = path_fn(o->d, rule, fp64);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
     const size_t smem = path_smem_bytes(a, rule, fp64, o->d);
@@ -172,7 +182,7 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     TRY(path_blocks_per_sm(fn, o->device, smem, &bps));
     long long blocks = (max_units + (kBlock / 32) - 1) / (kBlock / 32);
     long long cap = (long long)o->sm_count * bps;
-    const bool coop = rule == R_NEWTON_COOP;
+    const bool coop = rule == R_NEWTON_COOP || rule == R_NEWTON_COOP3;
     if (coop) cap = std::max(1LL, cap / std::max(1, o->grid_share));
     blocks = std::max(1LL, std::min(blocks, cap));
     void* args[] = {&a};
@@ -274,9 +284,9 @@ void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
     a.fitted = o->fitted.as<int>();
     if (o->rule_kind == R_IZ) {
         a.rule_src = fp64 ? (const void*)o->coef_d.p : (const void*)o->coef_f.p;
-        a.rule_stride = o->n_bnd * iz_stage_stride(o->d);
+        a.rule_stride = o->n_bnd * iz_stride(o->d, o->degree);
         a.n_bnd = o->n_bnd;
-        a.n_coef = iz_stage_stride(o->d);
+        a.n_coef = iz_stride(o->d, o->degree);
     } else if (o->rule_kind == R_CMC) {
         a.rule_src = fp64 ? (const void*)o->rec_d.p : (const void*)o->rec_f.p;
         a.rule_stride = o->rec_len;
@@ -291,7 +301,7 @@ bap_status set_rule_iz(bap_option* o, int degree) {
     o->degree = degree;
     o->n_coef = n_basis(s, degree);
     const size_t nc = (size_t)(o->n_dates + 1) * o->n_bnd * o->n_coef;
-    const size_t ns = (size_t)(o->n_dates + 1) * o->n_bnd * iz_stage_stride(o->d);
+    const size_t ns = (size_t)(o->n_dates + 1) * o->n_bnd * iz_stride(o->d, degree);
     TRY(o->coef64.reserve(nc * 8));
     TRY(o->coef_f.reserve(ns * 4));
     TRY(o->coef_d.reserve(ns * 8));
@@ -715,9 +725,11 @@ bap_status preload_kernels(int device) {
     {
         std::lock_guard<std::mutex> lk2(g_fn_mu);
         for (int D = 1; D <= MAXD; ++D) {
-            for (int rule : {(int)R_NONE, (int)R_IZ, (int)R_CMC, R_NEWTON_COOP}) {
-                for (int fp64 = 0; fp64 < (rule == R_NEWTON_COOP ? 1 : 2); ++fp64) {
+            for (int rule : {(int)R_NONE, (int)R_IZ, (int)R_CMC, R_NEWTON_COOP, R_IZ3, R_NEWTON_COOP3}) {
+                const bool coop = rule == R_NEWTON_COOP || rule == R_NEWTON_COOP3;
+                for (int fp64 = 0; fp64 < (coop ? 1 : 2); ++fp64) {
                     const void* fn = path_fn(D, rule, fp64 != 0);
+                    if (!fn) continue;            // no cubic kernels above MAXD_CUBIC
                     TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
                 }
             }
@@ -844,13 +856,14 @@ void option_destroy(bap_option* o) {
     if (own) cudaStreamDestroy(own);
 }
 
-bap_status validate_iz(const bap_option* o, const bap_iz_params* p) {
-    (void)o;
+bap_status validate_iz(int d, const bap_iz_params* p) {
     if (!p) return fail(BAP_EINVAL, "null argument");
     if (p->J < 1 || p->J > 8192) return fail(BAP_EINVAL, "J=%d outside 1..8192", p->J);
     if (p->N1 < 1 || p->N1 > (1LL << 31)) return fail(BAP_EINVAL, "N1 outside 1..2^31");
     if (p->max_iter < 1 || p->max_iter > 200) return fail(BAP_EINVAL, "max_iter outside 1..200");
-    if (p->degree < 0 || p->degree > 2) return fail(BAP_EINVAL, "degree outside 0..2");
+    if (p->degree < 0 || p->degree > 3) return fail(BAP_EINVAL, "degree outside 0..3");
+    if (p->degree == 3 && d > MAXD_CUBIC)
+        return fail(BAP_EINVAL, "cubic boundaries need d <= %d", MAXD_CUBIC);
     if (!(p->f_tol >= 0) || !(p->x_tol >= 0)) return fail(BAP_EINVAL, "negative tolerance");
     if (p->fixed_point && !(p->fp_eps > 0)) return fail(BAP_EINVAL, "fp_eps must be positive");
     return BAP_OK;
@@ -1266,7 +1279,7 @@ void bap_destroy(bap_option* o) { option_destroy(o); }
 bap_status bap_fit_boundary(bap_option* o, const bap_iz_params* p) {
     clear_error();
     if (!o) return fail(BAP_EINVAL, "null option");
-    TRY(validate_iz(o, p));
+    TRY(validate_iz(o->d, p));
     TRY(enqueue_fit_iz(o, p));
     CU(cudaStreamSynchronize(o->stream));
     return finish_fit_iz(o);
@@ -1445,7 +1458,8 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
     }
     if (kind == R_IZ) {
         const int degree = (int)buf[3];
-        if (degree < 0 || degree > 2) return fail(BAP_EINVAL, "bad degree");
+        if (degree < 0 || degree > 3 || (degree == 3 && o->d > MAXD_CUBIC))
+            return fail(BAP_EINVAL, "bad degree");
         TRY(set_rule_iz(o, degree));
         if ((int)buf[2] != o->n_bnd || (int)buf[4] != o->n_coef) return fail(BAP_EINVAL, "boundary shape mismatch");
         const size_t nc = (size_t)nd * o->n_bnd * o->n_coef;
@@ -1589,7 +1603,7 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     a.out_sums = d_sums;
     a.out_steps = reinterpret_cast<long long*>(d_steps);
 
-    const int rule = o->rule_kind;
+    const int rule = kernel_rule(o, o->rule_kind);
     const void* fn = path_fn(o->d, rule, false);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
     const size_t smem = path_smem_bytes(a, rule, false, o->d);

@@ -163,20 +163,51 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
 
 __device__ void stage_iz_one(const double* c, int s, int degree, double K, float* out_f,
                              double* out_d) {
-    const int stride = iz_stage_stride(s + 1);
+    // x = K B(y/K) with B = sum of c_i times the monomials of y/K: in price units the constant
+    // is K c_0, the linear terms keep c_t, the quadratic c_tu / K, the cubic c_tuv / K^2.  Nested
+    // for Horner: c_0, then for each t: c_t and, for each u >= t, c_tu followed (cubic) by its
+    // c_tuv for v >= u; the evaluation is
+    //   B = c_0 + sum_t y_t (c_t + sum_{u>=t} y_u (c_tu + sum_{v>=u} y_v c_tuv)).
+    const int stride = iz_stride(s + 1, degree);
     for (int i = 0; i < stride; ++i) { out_f[i] = 0.f; out_d[i] = 0.0; }
     out_f[0] = (float)(K * c[0]);
     out_d[0] = K * c[0];
-    int o = 1, qidx = 1 + s;
+    // positions of the quadratic and cubic coefficients in the basis order [1, y_a, y_a y_b
+    // (a <= b), y_a y_b y_c (a <= b <= c)]
+    const int q0 = 1 + s, c0 = 1 + s + s * (s + 1) / 2;
+    auto qpos = [&](int t, int u) {        // index of y_t y_u, t <= u
+        int k = 0;
+        for (int a = 0; a < t; ++a) k += s - a;
+        return q0 + k + (u - t);
+    };
+    auto cpos = [&](int t, int u, int v) { // index of y_t y_u y_v, t <= u <= v
+        int k = 0;
+        for (int a = 0; a < s; ++a)
+            for (int b = a; b < s; ++b)
+                for (int e = b; e < s; ++e) {
+                    if (a == t && b == u && e == v) return c0 + k;
+                    ++k;
+                }
+        return c0;
+    };
+    int o = 1;
     for (int t = 0; t < s; ++t) {
         const double lin = degree >= 1 ? c[1 + t] : 0.0;
         out_f[o] = (float)lin;
         out_d[o] = lin;
         ++o;
-        for (int u = t; u < s; ++u, ++o) {
-            const double q = degree >= 2 ? c[qidx++] / K : 0.0;
+        for (int u = t; u < s; ++u) {
+            const double q = degree >= 2 ? c[qpos(t, u)] / K : 0.0;
             out_f[o] = (float)q;
             out_d[o] = q;
+            ++o;
+            if (degree >= 3) {
+                for (int v = u; v < s; ++v, ++o) {
+                    const double cu = c[cpos(t, u, v)] / (K * K);
+                    out_f[o] = (float)cu;
+                    out_d[o] = cu;
+                }
+            }
         }
     }
 }
@@ -185,7 +216,7 @@ __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, in
                                 int degree, double K, float* coef_f, double* coef_d) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (n_dates + 1) * n_bnd) return;
-    const size_t so = (size_t)i * iz_stage_stride(s + 1);
+    const size_t so = (size_t)i * iz_stride(s + 1, degree);
     stage_iz_one(coef64 + (size_t)i * n_coef, s, degree, K, coef_f + so, coef_d + so);
 }
 
@@ -195,10 +226,11 @@ __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, in
 // mean); no points -> "never exercise".  Normal equations on the diagonally equilibrated Gram
 // matrix, solved by Cholesky; a Cholesky failure also falls back to the mean.
 
-__device__ inline double basis_val(const double* y, int bi, int bj) {
+__device__ inline double basis_val(const double* y, int bi, int bj, int bk) {
     const double a = bi < 0 ? 1.0 : y[bi];
     const double b = bj < 0 ? 1.0 : y[bj];
-    return a * b;
+    if (bk < 0) return a * b;
+    return a * b * y[bk];
 }
 
 __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, int m, int J, int n_bnd, int degree, int n_coef,
@@ -208,7 +240,7 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
     const int d = M->d, s = d - 1;
     const int p = n_bnd > 1 ? b : 0;
     const double K = M->K;
-    __shared__ int bi[MAXCOEF], bj[MAXCOEF];
+    __shared__ int bi[MAXCOEF], bj[MAXCOEF], bk[MAXCOEF];
     __shared__ double G[MAXCOEF * MAXCOEF];
     __shared__ double rhs[MAXCOEF];
     __shared__ double red[32];
@@ -217,12 +249,16 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
     const int P = n_coef;
     if (threadIdx.x == 0) {
         int o = 0;
-        bi[o] = -1; bj[o] = -1; ++o;
+        bi[o] = -1; bj[o] = -1; bk[o] = -1; ++o;
         if (degree >= 1)
-            for (int t = 0; t < s; ++t) { bi[o] = t; bj[o] = -1; ++o; }
+            for (int t = 0; t < s; ++t) { bi[o] = t; bj[o] = -1; bk[o] = -1; ++o; }
         if (degree >= 2)
             for (int t = 0; t < s; ++t)
-                for (int u = t; u < s; ++u) { bi[o] = t; bj[o] = u; ++o; }
+                for (int u = t; u < s; ++u) { bi[o] = t; bj[o] = u; bk[o] = -1; ++o; }
+        if (degree >= 3)
+            for (int t = 0; t < s; ++t)
+                for (int u = t; u < s; ++u)
+                    for (int v = u; v < s; ++v) { bi[o] = t; bj[o] = u; bk[o] = v; ++o; }
     }
     __syncthreads();
     // count of used points and their mean
@@ -292,7 +328,7 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
                         int u = 0;
                         for (int q = 0; q < d; ++q)
                             if (q != p) y[u++] = S[q] / K;
-                        for (int r = 0; r < P; ++r) Bs[t][r] = basis_val(y, bi[r], bj[r]);
+                        for (int r = 0; r < P; ++r) Bs[t][r] = basis_val(y, bi[r], bj[r], bk[r]);
                         Bs[t][P] = state[item].x / K;
                     }
                 }
@@ -372,7 +408,7 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
         }
         const size_t o = ((size_t)m * n_bnd + b) * P;
         for (int i = 0; i < P; ++i) coef64[o + i] = coef[i];
-        const size_t so = ((size_t)m * n_bnd + b) * iz_stage_stride(d);
+        const size_t so = ((size_t)m * n_bnd + b) * iz_stride(d, degree);
         stage_iz_one(coef64 + o, s, degree, K, coef_f + so, coef_d + so);
         if (b == 0) fitted[m] = 1;
     }

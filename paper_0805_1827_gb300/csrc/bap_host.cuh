@@ -173,7 +173,7 @@ bap_status option_alloc(bap_option** out);
 bap_status option_load(bap_option* o, const DevModel& hm);
 bap_status option_create(const bap_model* md, bap_option** out);
 void option_destroy(bap_option* o);
-bap_status validate_iz(const bap_option* o, const bap_iz_params* p);
+bap_status validate_iz(int d, const bap_iz_params* p);
 bap_status validate_cmc(const bap_option* o, const bap_cmc_params* p);
 bap_status validate_price(const bap_option* o, int64_t n_paths);
 // Enqueue on the option's stream; the matching finish_* reads the results once the stream has

@@ -12,13 +12,19 @@ namespace bap {
 constexpr int MAXD = BAP_MAX_D;
 constexpr int MAXF = MAXD + 1;            // CMC features: d prices + the payoff
 constexpr int MAXDATES = BAP_MAX_DATES;
-constexpr int MAXCOEF = 1 + (MAXD - 1) + (MAXD - 1) * MAXD / 2;   // quadratic in d-1 variables
+// Boundary coefficients: the full quadratic in d-1 <= 9 variables (55), or the full cubic in
+// d-1 <= 5 variables (56; cubic boundaries are offered up to d = MAXD_CUBIC).
+constexpr int MAXD_CUBIC = 6;
+constexpr int MAXCOEF = 56;
 constexpr int WARP = 32;
 
 enum Purpose : uint32_t { P_IZ = 1, P_CMC = 2, P_TRAIN = 3, P_PRICE = 4 };
 enum RuleKind : int { R_NONE = 0, R_IZ = 1, R_CMC = 2 };
-// Kernel selector (not a rule kind): the cooperative kernel that runs all Newton passes of a date.
+// Kernel selectors (not rule kinds): the cooperative kernel that runs all Newton passes of a date,
+// and the I&Z kernels for cubic boundaries (one pass, cooperative).
 constexpr int R_NEWTON_COOP = 3;
+constexpr int R_IZ3 = 4;
+constexpr int R_NEWTON_COOP3 = 5;
 enum Mode : int { MODE_SUMS = 0, MODE_NEWTON = 1, MODE_LABEL = 2, MODE_TRACE = 3 };
 enum ItemStatus : int { ST_OK = 0, ST_NOCONV = 1, ST_NOROOT = 2 };
 
@@ -172,6 +178,7 @@ __host__ __device__ inline int n_basis(int s, int degree) {
     int n = 1;
     if (degree >= 1) n += s;
     if (degree >= 2) n += s * (s + 1) / 2;
+    if (degree >= 3) n += s * (s + 1) * (s + 2) / 6;
     return n;
 }
 
@@ -180,6 +187,17 @@ __host__ __device__ inline int n_basis(int s, int degree) {
 // block is read with 16-byte vector loads.
 __host__ __device__ constexpr int iz_stage_stride(int d) {
     return ((1 + (d - 1) + (d - 1) * d / 2) + 3) & ~3;
+}
+
+// The same for a cubic boundary: the full cubic in the d-1 other assets, nested for Horner
+// evaluation (see stage_iz_one), padded to a multiple of 4.
+__host__ __device__ constexpr int iz_stage_stride3(int d) {
+    return ((1 + (d - 1) + (d - 1) * d / 2 + (d - 1) * d * (d + 1) / 6) + 3) & ~3;
+}
+
+// Staged stride of a boundary of this degree.
+__host__ __device__ constexpr int iz_stride(int d, int degree) {
+    return degree >= 3 ? iz_stage_stride3(d) : iz_stage_stride(d);
 }
 
 // CMC staged rule record per date (floats or doubles; counts and offsets stored as values):

@@ -299,7 +299,7 @@ template <int D, int RULE, typename Real, bool COOP>
 __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NF = D + 1;
-    constexpr int P4 = iz_stage_stride(D);
+    constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
     const int rule_len = (RULE == R_NONE) ? 0 : (nk - 1) * a.rule_stride;   // dates m+1..NT-1
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
@@ -477,7 +477,35 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                                 }
                             }
                             ex = is_put ? (sp <= B) : (sp >= B);
-                        } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
+                    } else if (RULE == R_IZ3) {
+                            // the same test with a cubic boundary (nested Horner order); the
+                            // coefficients are read from shared memory as they are used
+                            const int p = is_max ? imax : 0;
+                            Real sp = S[0];
+#pragma unroll
+                            for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
+                            const Real* cc = sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4;
+                            Real B = cc[0];
+                            if constexpr (D > 1) {
+                                Real y[D - 1];
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
+                                int idx = 1;
+#pragma unroll
+                                for (int t = 0; t < D - 1; ++t) {
+                                    Real acc_t = cc[idx++];
+#pragma unroll
+                                    for (int u = t; u < D - 1; ++u) {
+                                        Real acc_u = cc[idx++];
+#pragma unroll
+                                        for (int v = u; v < D - 1; ++v) acc_u = fma(cc[idx++], y[v], acc_u);
+                                        acc_t = fma(acc_u, y[u], acc_t);
+                                    }
+                                    B = fma(acc_t, y[t], B);
+                                }
+                            }
+                            ex = is_put ? (sp <= B) : (sp >= B);
+                    } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
                             const Real* rec = sh_rule + kr * a.rule_stride;
                             Real F = rec[0];
 #pragma unroll

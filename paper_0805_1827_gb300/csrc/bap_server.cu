@@ -293,7 +293,7 @@ bap_status bap_submit(bap_server* s, const bap_model* md, int method, const void
     bap_status st = BAP_OK;
     if (method == BAP_METHOD_IZ) {
         r->iz = *static_cast<const bap_iz_params*>(params);
-        st = validate_iz(nullptr, &r->iz);
+        st = validate_iz(r->hm.d, &r->iz);
     } else {
         r->cmc = *static_cast<const bap_cmc_params*>(params);
         st = validate_cmc(nullptr, &r->cmc);

@@ -241,3 +241,36 @@ def test_european_limit_against_black_scholes():
     r = opt.price(1_000_000, 7)
     assert abs(r["price"] - bs_price(100, 100, 0.05, 0.0, 0.2, 1.0, call=False)) < 3 * r["se"]
     opt.close()
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_fit_cubic_boundary(d):
+    """Cubic boundaries (Section 2.2): the device fit and pricing against the oracle's, and the
+    staged cubic Horner form against the oracle's plain polynomial (exercise decisions)."""
+    spec = spec_max_call(d, 100.0, rho=0.2, n_dates=5, T=1.5)
+    params = IZParams(J=64, N1=8000, degree=3, seed=2)
+    _iz_fit_compare(spec, params, 100_000, 4)
+
+
+def test_cubic_boundary_limits():
+    opt = bap.Option(spec_max_call(7, 100.0, rho=0.2, n_dates=3, T=1.0))
+    with pytest.raises(bap.BapError) as e:
+        opt.fit_boundary(IZParams(J=8, N1=100, degree=3, seed=1))
+    assert e.value.status == bap.BAP_EINVAL
+    with pytest.raises(bap.BapError) as e:
+        opt.fit_boundary(IZParams(J=8, N1=100, degree=4, seed=1))
+    assert e.value.status == bap.BAP_EINVAL
+    opt.close()
+
+
+def test_cubic_rules_round_trip():
+    spec = spec_max_call(3, 100.0, rho=0.2, n_dates=5, T=1.5)
+    a = bap.Option(spec)
+    a.fit_boundary(IZParams(J=32, N1=4000, degree=3, seed=5))
+    buf = a.export_rules()
+    b = bap.Option(spec)
+    b.import_rules(buf)
+    ra, rb = a.price(100_000, 9), b.price(100_000, 9)
+    assert ra["price"] == rb["price"] and ra["var"] == rb["var"]
+    a.close()
+    b.close()
