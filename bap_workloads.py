@@ -91,6 +91,8 @@ class CMCParams:
     seed: int = 0
     sampler: int = 0          # training points: 0 independent per date, 1 Brownian bridge back
                               # from the last fitted date (Section 3.3)
+    boost: int = 0            # classifier: 0 discrete AdaBoost, 1 LogitBoost (n_stumps = rounds,
+                              # stored as two vote stumps each)
 
 
 def equicorrelation(d: int, rho: float) -> np.ndarray:

@@ -105,6 +105,11 @@ typedef struct bap_cmc_params {
                                  per date; 1 one set of J points walked back from the last
                                  fitted date by a Brownian bridge (Section 3.3), each date's
                                  bridge normals being those the independent draw would use */
+    int boost;                /* classifier (Section 3.2: "AdaBoost or LogitBoost"): 0 discrete
+                                 AdaBoost on stumps; 1 LogitBoost with regression stumps (then
+                                 n_stumps counts rounds, 1..BAP_MAX_STUMPS/2, each stored as a
+                                 threshold stump and a constant; J <= 4096; runs on a cluster of
+                                 d+1 blocks, EINVAL if the device cannot place it) */
 } bap_cmc_params;
 
 typedef struct bap_result {

@@ -615,10 +615,74 @@ def adaboost(Fx: np.ndarray, labels: np.ndarray, n_stumps: int):
     return out
 
 
+LB_FIX = 2.0 ** 48     # fixed-point scale of LogitBoost's weighted sums
+LB_ZMAX = 4.0          # working responses are clamped to [-LB_ZMAX, LB_ZMAX]
+
+
+def logitboost(Fx: np.ndarray, labels: np.ndarray, n_rounds: int):
+    """Two-class LogitBoost with regression stumps (Section 3.2 names LogitBoost beside
+    AdaBoost; the algorithm of Friedman, Hastie and Tibshirani, Ann. Statist. 28 (2000)):
+    F = 0; each round p = 1 / (1 + e^{-2F}), w = p (1 - p), z = (y* - p) / w clamped to
+    [-4, 4] (y* = 1 for label +1, else 0), then the weighted least-squares regression stump
+    f(x) = c_L for x_f <= t, c_R above, and F <- F + f / 2.
+
+    The stump search sums w and w z in order of each feature in fixed point (round(v 2^48),
+    exact), so the choice does not depend on summation order: a split after sorted position
+    i between distinct values gains S_L^2 / W_L + S_R^2 / W_R (FP64 from the exact sums;
+    no split gains S^2 / W); with G the largest gain the first candidate in (no split, then
+    feature, threshold ascending) order with gain >= G (1 - 1e-12) wins; c = S / W per side.
+    Returns the rounds as (feature, threshold, c_L, c_R), threshold -inf for no split."""
+    J, nf = Fx.shape
+    ys = (labels > 0).astype(np.float64)
+    F = np.zeros(J)
+    orders = [np.argsort(Fx[:, f], kind="stable") for f in range(nf)]
+    out = []
+    for _ in range(n_rounds):
+        p = 1.0 / (1.0 + np.exp(-2.0 * F))
+        w = p * (1.0 - p)
+        z = np.clip((ys - p) / w, -LB_ZMAX, LB_ZMAX)
+        wq = np.rint(w * LB_FIX).astype(np.int64)
+        sq = np.rint(w * z * LB_FIX).astype(np.int64)
+        W, S = int(wq.sum()), int(sq.sum())
+        if W <= 0:
+            break
+        cands = [(float(S) * float(S) / float(W), 0, -math.inf, float(S) / float(W),
+                  float(S) / float(W))]
+        for f in range(nf):
+            o = orders[f]
+            v = Fx[o, f]
+            cw, cs = np.cumsum(wq[o])[:-1], np.cumsum(sq[o])[:-1]    # left of each split
+            WL, SL = cw.astype(np.float64), cs.astype(np.float64)
+            WR, SR = (W - cw).astype(np.float64), (S - cs).astype(np.float64)
+            ok = (v[1:] > v[:-1]) & (cw > 0) & (W - cw > 0)
+            for i in np.flatnonzero(ok):
+                g = SL[i] * SL[i] / WL[i] + SR[i] * SR[i] / WR[i]
+                cands.append((g, f, 0.5 * (v[i] + v[i + 1]), SL[i] / WL[i], SR[i] / WR[i]))
+        G = max(c[0] for c in cands)
+        _, f, thr, cl, cr = next(c for c in cands if c[0] >= G * (1.0 - 1e-12))
+        F = F + 0.5 * np.where(Fx[:, f] > thr, cr, cl)
+        out.append((int(f), float(thr), float(cl), float(cr)))
+    return out
+
+
+def logit_to_stumps(rounds):
+    """A LogitBoost round f/2 = c_L/2 below t, c_R/2 above, written as two vote stumps of the
+    rule format: A + B sign(x - t) with A = (c_L + c_R)/4 (a constant stump, threshold -inf) and
+    B = (c_R - c_L)/4 (polarity = sign of B, weight |B|)."""
+    out = []
+    for f, thr, cl, cr in rounds:
+        B = 0.25 * (cr - cl)
+        A = 0.25 * (cl + cr)
+        out.append((f, thr, 1 if B >= 0 else -1, abs(B)))
+        out.append((f, -math.inf, 1 if A >= 0 else -1, abs(A)))
+    return out
+
+
 def cmc_fit(spec: OptionSpec, params: CMCParams, n_threads: int = 0, precision: str = "f64",
             last_date_only: bool = False):
     """Picazo CMC fit (Algorithm 2 without the final [mc])."""
-    rules = empty_cmc_rules(spec, params.n_stumps)
+    logit = getattr(params, "boost", 0) == 1
+    rules = empty_cmc_rules(spec, params.n_stumps * (2 if logit else 1))
     diag = {}
     dates = range(spec.n_dates - 1, 0, -1)
     if last_date_only:
@@ -637,7 +701,8 @@ def cmc_fit(spec: OptionSpec, params: CMCParams, n_threads: int = 0, precision: 
         yv = phi - Cv
         lab = np.where(yv > 0, 1, -1)
         Fx = np.concatenate([X, phi[:, None]], axis=1)
-        st = adaboost(Fx, lab, params.n_stumps)
+        st = (logit_to_stumps(logitboost(Fx, lab, params.n_stumps)) if logit
+              else adaboost(Fx, lab, params.n_stumps))
         rules.n_stumps[m] = len(st)
         for i, (f, thr, pol, a) in enumerate(st):
             rules.feat[m, i] = f

@@ -56,7 +56,7 @@ class _IZ(C.Structure):
 
 class _CMC(C.Structure):
     _fields_ = [("J", C.c_int), ("N2", C.c_int64), ("n_stumps", C.c_int), ("seed", C.c_uint64),
-                ("sampler", C.c_int)]
+                ("sampler", C.c_int), ("boost", C.c_int)]
 
 
 class _Result(C.Structure):
@@ -173,7 +173,7 @@ def _params(p):
     if hasattr(p, "N1"):
         return 0, _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point,
                       p.fp_eps)
-    return 1, _CMC(p.J, p.N2, p.n_stumps, p.seed, getattr(p, "sampler", 0))
+    return 1, _CMC(p.J, p.N2, p.n_stumps, p.seed, getattr(p, "sampler", 0), getattr(p, "boost", 0))
 
 
 class Option:
@@ -225,7 +225,7 @@ class Option:
         return _check(lib().bap_fit_boundary(self.h, C.byref(c)), (BAP_OK, BAP_ENOCONV))
 
     def fit_classifier(self, p) -> int:
-        c = _CMC(p.J, p.N2, p.n_stumps, p.seed, getattr(p, "sampler", 0))
+        c = _CMC(p.J, p.N2, p.n_stumps, p.seed, getattr(p, "sampler", 0), getattr(p, "boost", 0))
         return _check(lib().bap_fit_classifier(self.h, C.byref(c)))
 
     def price(self, n_paths: int, seed: int) -> dict:

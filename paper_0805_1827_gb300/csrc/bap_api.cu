@@ -736,10 +736,12 @@ bap_status preload_kernels(int device) {
         }
         const void* ab = (const void*)adaboost_kernel;
         TRY(raise_smem_limit(ab, device, g_fn[{ab, device}]));
-        const void* abc = (const void*)adaboost_cluster_kernel;
-        TRY(raise_smem_limit(abc, device, g_fn[{abc, device}]));
-        // d + 1 features up to 11 blocks per cluster: above the portable 8
-        CU(cudaFuncSetAttribute(abc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        // the cluster boosting kernels: d + 1 features up to 11 blocks per cluster, above the
+        // portable 8
+        for (const void* fn : {(const void*)adaboost_cluster_kernel, (const void*)logitboost_cluster_kernel}) {
+            TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+            CU(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        }
     }
     const void* others[] = {
         (const void*)iota_kernel,          (const void*)korobov_merit_kernel,
@@ -876,6 +878,9 @@ bap_status validate_cmc(const bap_option* o, const bap_cmc_params* p) {
     if (p->N2 < 1 || p->N2 > (1LL << 31)) return fail(BAP_EINVAL, "N2 outside 1..2^31");
     if (p->n_stumps < 1 || p->n_stumps > BAP_MAX_STUMPS) return fail(BAP_EINVAL, "n_stumps outside 1..%d", BAP_MAX_STUMPS);
     if (p->sampler != 0 && p->sampler != 1) return fail(BAP_EINVAL, "sampler outside 0..1");
+    if (p->boost != 0 && p->boost != 1) return fail(BAP_EINVAL, "boost outside 0..1");
+    if (p->boost == 1 && (p->n_stumps > BAP_MAX_STUMPS / 2 || p->J > 4096))
+        return fail(BAP_EINVAL, "LogitBoost: rounds 1..%d and J <= 4096", BAP_MAX_STUMPS / 2);
     return BAP_OK;
 }
 
@@ -1000,19 +1005,21 @@ void boost_cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, in
     cfg.numAttrs = 1;
 }
 
-// Whether a cluster of nF such blocks fits on the device (cached per device, nF and size).
-bap_status boost_cluster_fits(int device, int nF, size_t smem, cudaStream_t st, bool* ok) {
+// Whether a cluster of nF blocks of this boosting kernel fits on the device (cached per kernel,
+// device, nF and size).
+bap_status boost_cluster_fits(const void* fn, int device, int nF, size_t smem, cudaStream_t st,
+                              bool* ok) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, size_t>, bool> known;
+    static std::map<std::tuple<const void*, int, int, size_t>, bool> known;
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_tuple(device, nF, smem);
+    const auto key = std::make_tuple(fn, device, nF, smem);
     auto it = known.find(key);
     if (it == known.end()) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         boost_cluster_config(cfg, attr, nF, smem, st);
         int n = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, (const void*)adaboost_cluster_kernel, &cfg);
+        const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
         if (e != cudaSuccess) cudaGetLastError();
         it = known.emplace(key, e == cudaSuccess && n >= 1).first;
     }
@@ -1025,7 +1032,8 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     o->launches = o->path_launches = 0;
     o->prof_used = 0;
     o->phase_used = 0;
-    TRY(set_rule_cmc(o, p->n_stumps));
+    const bool logit = p->boost == 1;
+    TRY(set_rule_cmc(o, logit ? 2 * p->n_stumps : p->n_stumps));
     o->method = 1;
     cudaStream_t st = o->stream;
     if (o->n_dates < 2) {
@@ -1062,7 +1070,17 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     const size_t abc_smem = (size_t)J * 10 + std::max((size_t)P2 * 12, (size_t)J * 16) + 4 +
                             8 * (size_t)((J + 31) / 32);
     bool cluster = false;
-    if (o->boost_form == 1) TRY(boost_cluster_fits(o->device, nF, abc_smem, st, &cluster));
+    // LogitBoost: one cluster of nF blocks (the slices of F, the sums, both permutations)
+    const size_t ns_lb = (size_t)((J + nF - 1) / nF);
+    const size_t lb_smem = ns_lb * 8 + std::max((size_t)P2 * 12, (size_t)J * 24) + 2 * (size_t)J + 4 +
+                           4 * (size_t)((J + 31) / 32);
+    if (logit) {
+        TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, lb_smem, st, &cluster));
+        if (!cluster)
+            return fail(BAP_EINVAL, "LogitBoost needs a cluster of %d blocks with %zu B of shared memory each", nF, lb_smem);
+    } else if (o->boost_form == 1) {
+        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, st, &cluster));
+    }
     o->last_boost_cluster = cluster ? 1 : 0;
     {
         std::lock_guard<std::mutex> lk(g_fn_mu);
@@ -1100,7 +1118,18 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         phase_end(o, ph_calc);
         TRY(sl);
         const int ph_fit = phase_begin(o, PH_FIT);
-        if (cluster) {
+        if (logit) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            boost_cluster_config(cfg, attr, nF, lb_smem, st);
+            CU(cudaLaunchKernelEx(&cfg, logitboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
+                                  m, J, (const double*)o->start.as<double>(),
+                                  (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
+                                  o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
+                                  o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+                                  o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
+                                  o->rec_d.as<double>(), o->fitted.as<int>()));
+        } else if (cluster) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             boost_cluster_config(cfg, attr, nF, abc_smem, st);
@@ -1211,7 +1240,7 @@ size_t estimate_bytes(const bap_model* md, int method, const void* params, int64
         n = (size_t)p->J;
         C = (size_t)((p->N2 + choose_chunk((long long)n, p->N2) - 1) / choose_chunk((long long)n, p->N2));
         extra = (d + 1) * n * 20 + d * n * 8;     // sorted features, bridge state
-        rules = nd * (size_t)p->n_stumps * 64;
+        rules = nd * (size_t)p->n_stumps * (p->boost == 1 ? 2 : 1) * 64;
     }
     const size_t items = n * (d * 8 + sizeof(ItemState) + 40) + n * C * 32 + nd * n * 16;
     const size_t price_c = (size_t)((n_paths + choose_chunk(1, n_paths) - 1) / choose_chunk(1, n_paths));

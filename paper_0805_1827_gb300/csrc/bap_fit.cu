@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
     __shared__ long long red_a[32], red_b[32], red_m[32];
     __shared__ double red_d[32];
     __shared__ long long s_neg[MAXF];
-    __shared__ double s_alpha, s_thr, s_fok, s_fbad;
+    __shared__ double s_thr, s_fok, s_fbad;
     __shared__ int s_f, s_pol, s_stop, s_count;
     const int tid = threadIdx.x;
 
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
                 thr[o_st + k] = th;
                 pol[o_st + k] = pl;
                 alpha[o_st + k] = al;
-                s_f = f; s_thr = th; s_pol = pl; s_alpha = al;
+                s_f = f; s_thr = th; s_pol = pl;
                 s_fok = exp(-al);
                 s_fbad = exp(al);
                 if (eps <= 1e-10) s_stop = 2;
@@ -1089,6 +1089,240 @@ __global__ void __launch_bounds__(512) adaboost_cluster_kernel(
             __syncthreads();
         }
         if (s_stop == 2) break;
+    }
+    if (f == 0 && tid == 0) {
+        n_stumps[m] = count;
+        stage_cmc_one(nF, count, feat + o_st, thr + o_st, pol + o_st, alpha + o_st, rec_len,
+                      rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
+        fitted[m] = 1;
+    }
+    cluster.sync();           // the leader's exchange area and the masks stay until all are done
+}
+
+// ---------------------------------------------------------------------------------------------
+// [class] LogitBoost (Section 3.2 names it beside AdaBoost) with regression stumps on a
+// thread-block cluster, block f owning feature f.  Each round: p = 1 / (1 + e^{-2F}),
+// w = p (1 - p), z = (y* - p) / w clamped to [-4, 4]; the stump of largest weighted
+// least-squares gain S_L^2 / W_L + S_R^2 / W_R over the splits between distinct sorted values
+// (no split: S^2 / W), the first within a relative 1e-12 of the largest in (no split, feature,
+// threshold) order; leaves c = S / W; F <- F + f / 2.  The sums of w and w z are exact in 2^48
+// fixed point.  The FP64 exp of p is the costly part: block f computes it for its own slice of
+// the points and the blocks gather each other's slices through distributed shared memory.  A
+// round is stored as two vote stumps (threshold stump |B|, constant |A|; A = (c_L + c_R) / 4,
+// B = (c_R - c_L) / 4), so the rule staging and the path kernel are the AdaBoost ones.
+
+constexpr double kLbFix = 281474976710656.0;      // 2^48
+constexpr double kLbZmax = 4.0;
+
+struct LogitExchange {
+    long long W, S;                 // round totals (the leader's)
+    unsigned long long gmax[MAXF];  // largest gain per feature (bit pattern of a double >= 0)
+    int cand[MAXF];                 // first split position within the tolerance, -1 none
+    double cthr[MAXF], ccl[MAXF], ccr[MAXF];
+};
+
+__global__ void __launch_bounds__(512) logitboost_cluster_kernel(
+    const DevModel* M, int m, int J, const double* X, const int* label, int n_rounds,
+    double* sorted_v, int* sorted_i, int max_stumps, int* n_stumps, int* feat, double* thr,
+    int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d, int* fitted) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned FULL = 0xffffffffu;
+    const int d = M->d;
+    const int nF = d + 1;
+    const int f = (int)cluster.block_rank();
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    const int nwords = (J + 31) / 32;
+    const int ns = (J + nF - 1) / nF;                // slice of points whose p this block computes
+    const int s_lo = f * ns, s_hi = min(J, s_lo + ns);
+    // shared memory: F (slice) | region (sort keys, then wq, sq, six, inv) | ys | split | mask
+    double* Fs = reinterpret_cast<double*>(smem);                         // ns
+    unsigned char* region = smem + (size_t)ns * 8;
+    double* key = reinterpret_cast<double*>(region);
+    int* idx = reinterpret_cast<int*>(key + P2);
+    long long* wq = reinterpret_cast<long long*>(region);                  // J
+    long long* sq = wq + J;                                                 // J
+    int* six = reinterpret_cast<int*>(sq + J);                             // J
+    int* inv = six + J;                                                     // J
+    const size_t region_bytes = (size_t)P2 * 12 > (size_t)J * 24 ? (size_t)P2 * 12 : (size_t)J * 24;
+    unsigned char* ys = region + region_bytes;                              // J: y* in {0, 1}
+    unsigned char* split = ys + J;                                          // J
+    unsigned* mask = reinterpret_cast<unsigned*>(smem + ((size_t)ns * 8 + region_bytes + 2 * (size_t)J + 3) / 4 * 4);
+    __shared__ LogitExchange ex;
+    __shared__ long long red_a[32], red_b[32];
+    __shared__ unsigned long long s_gmax;
+    __shared__ int s_first, s_f, s_const, s_stop;
+    __shared__ double s_lim, s_thr, s_cl, s_cr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    LogitExchange* lead = cluster.map_shared_rank(&ex, 0);
+
+    for (int i = tid; i < P2; i += blockDim.x) {
+        key[i] = i < J ? cmc_feature(M, X, i, f) : INFINITY;
+        idx[i] = i < J ? i : 0x7fffffff;
+    }
+    __syncthreads();
+    block_bitonic(key, idx, P2);
+    for (int r = tid; r < J; r += blockDim.x) {
+        sorted_v[(size_t)f * J + r] = key[r];
+        sorted_i[(size_t)f * J + r] = idx[r];
+        split[r] = (r < J - 1 && key[r + 1] > key[r]) ? 1 : 0;
+    }
+    __syncthreads();
+    for (int r = tid; r < J; r += blockDim.x) {
+        const int k = sorted_i[(size_t)f * J + r];
+        six[r] = k;
+        inv[k] = r;
+    }
+    for (int i = tid; i < J; i += blockDim.x) ys[i] = label[i] > 0 ? 1 : 0;
+    for (int i = s_lo + tid; i < s_hi; i += blockDim.x) Fs[i - s_lo] = 0.0;
+    __threadfence();
+    cluster.sync();
+
+    const double* sv = sorted_v + (size_t)f * J;
+    const int per = (J + blockDim.x - 1) / blockDim.x;
+    const int lo = tid * per, hi = min(J, lo + per);
+    const size_t o_st = (size_t)m * max_stumps;
+    int count = 0;
+    for (int round = 0; round < n_rounds; ++round) {
+        // this block's slice of w and w z in fixed point
+        for (int i = s_lo + tid; i < s_hi; i += blockDim.x) {
+            const double p = 1.0 / (1.0 + exp(-2.0 * Fs[i - s_lo]));
+            const double w = p * (1.0 - p);
+            const double z = fmin(fmax(((double)ys[i] - p) / w, -kLbZmax), kLbZmax);
+            wq[i] = __double2ll_rn(w * kLbFix);
+            sq[i] = __double2ll_rn((w * z) * kLbFix);
+        }
+        if (tid == 0) { s_gmax = 0ULL; s_first = 0x7fffffff; }
+        cluster.sync();
+        // the other blocks' slices
+        for (int g = 0; g < nF; ++g) {
+            if (g == f) continue;
+            const long long* rw = cluster.map_shared_rank(wq, g);
+            const long long* rs = cluster.map_shared_rank(sq, g);
+            const int glo = g * ns, ghi = min(J, glo + ns);
+            for (int i = glo + tid; i < ghi; i += blockDim.x) {
+                wq[i] = rw[i];
+                sq[i] = rs[i];
+            }
+        }
+        __syncthreads();
+        // prefix sums over this feature's sorted order
+        long long pw = 0, ps = 0;
+        for (int r = lo; r < hi; ++r) {
+            const int k = six[r];
+            pw += wq[k];
+            ps += sq[k];
+        }
+        long long pw0 = pw, ps0 = ps, W = 0, S = 0;
+        block_scan2(pw0, ps0, red_a, red_b, W, S);
+        auto gain = [&](long long WL, long long SL) -> double {
+            const long long WR = W - WL, SR = S - SL;
+            return (double)SL * (double)SL / (double)WL + (double)SR * (double)SR / (double)WR;
+        };
+        unsigned long long my = 0ULL;
+        {
+            long long a = pw0, b = ps0;
+            for (int r = lo; r < hi; ++r) {
+                const int k = six[r];
+                a += wq[k];
+                b += sq[k];
+                if (split[r] && a > 0 && W - a > 0) {
+                    const unsigned long long gb = (unsigned long long)__double_as_longlong(gain(a, b));
+                    my = gb > my ? gb : my;
+                }
+            }
+        }
+        atomicMax(&s_gmax, my);
+        __syncthreads();
+        if (tid == 0) {
+            lead->gmax[f] = s_gmax;
+            if (f == 0) { ex.W = W; ex.S = S; }
+        }
+        cluster.sync();
+        // the overall largest gain (no split included), then this feature's first split within
+        // the tolerance; thread 0 reads the leader's values for the block
+        if (tid == 0) {
+            const long long Wl = lead->W, Sl = lead->S;
+            double G = Wl > 0 ? (double)Sl * (double)Sl / (double)Wl : 0.0;
+            for (int g = 0; g < nF; ++g) G = fmax(G, __longlong_as_double((long long)lead->gmax[g]));
+            s_lim = G * (1.0 - 1e-12);
+            s_const = (Wl > 0 && (double)Sl * (double)Sl / (double)Wl >= s_lim) ? 1 : 0;
+            s_stop = Wl > 0 ? 0 : 1;          // every weight rounded to 0: nothing to fit
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const double lim = s_lim;
+        int rfirst = 0x7fffffff;
+        long long a_at = 0, b_at = 0;
+        if (!s_const) {
+            long long a = pw0, b = ps0;
+            for (int r = lo; r < hi && rfirst == 0x7fffffff; ++r) {
+                const int k = six[r];
+                a += wq[k];
+                b += sq[k];
+                if (split[r] && a > 0 && W - a > 0 && gain(a, b) >= lim) {
+                    rfirst = r;
+                    a_at = a;
+                    b_at = b;
+                }
+            }
+            atomicMin(&s_first, rfirst);
+        }
+        __syncthreads();
+        const int rstar = s_const ? 0x7fffffff : s_first;
+        if (rfirst != 0x7fffffff && rfirst == rstar) {
+            lead->cand[f] = rstar;
+            lead->cthr[f] = 0.5 * (sv[rstar] + sv[rstar + 1]);
+            lead->ccl[f] = (double)b_at / (double)a_at;
+            lead->ccr[f] = (double)(S - b_at) / (double)(W - a_at);
+        } else if (tid == 0 && rstar == 0x7fffffff) {
+            lead->cand[f] = -1;
+        }
+        for (int wd = warp; wd < nwords; wd += nwarps) {
+            const int i = wd * 32 + lane;
+            const bool above = i < J && rstar != 0x7fffffff && inv[i] > rstar;
+            const unsigned bits = __ballot_sync(FULL, above);
+            if (lane == 0) mask[wd] = bits;
+        }
+        cluster.sync();
+        // the chosen stump (thread 0 reads the leader's values) and the update of F's slice
+        if (tid == 0) {
+            const long long Wl = lead->W, Sl = lead->S;
+            int cf = -1;
+            if (!s_const)
+                for (int g = 0; g < nF && cf < 0; ++g)
+                    if (lead->cand[g] >= 0) cf = g;
+            if (cf < 0) {
+                const double c = Wl > 0 ? (double)Sl / (double)Wl : 0.0;
+                s_f = 0; s_thr = -INFINITY; s_cl = c; s_cr = c;
+            } else {
+                s_f = cf; s_thr = lead->cthr[cf]; s_cl = lead->ccl[cf]; s_cr = lead->ccr[cf];
+            }
+            if (f == 0) {
+                const double B = 0.25 * (s_cr - s_cl), A = 0.25 * (s_cl + s_cr);
+                feat[o_st + count] = s_f;
+                thr[o_st + count] = s_thr;
+                pol[o_st + count] = B >= 0 ? 1 : -1;
+                alpha[o_st + count] = fabs(B);
+                feat[o_st + count + 1] = s_f;
+                thr[o_st + count + 1] = -INFINITY;
+                pol[o_st + count + 1] = A >= 0 ? 1 : -1;
+                alpha[o_st + count + 1] = fabs(A);
+            }
+        }
+        __syncthreads();
+        count += 2;
+        {
+            const double cl = s_cl, cr = s_cr;
+            const bool split_stump = !isinf(s_thr);
+            const unsigned* owner = cluster.map_shared_rank(mask, s_f);
+            for (int i = s_lo + tid; i < s_hi; i += blockDim.x) {
+                const bool above = split_stump ? ((owner[i >> 5] >> (i & 31)) & 1u) != 0 : true;
+                Fs[i - s_lo] += 0.5 * (above ? cr : cl);
+            }
+        }
     }
     if (f == 0 && tid == 0) {
         n_stumps[m] = count;

@@ -32,6 +32,11 @@ __global__ void adaboost_cluster_kernel(const DevModel* M, int m, int J, const d
                                         int* sorted_i, int max_stumps, int* n_stumps, int* feat,
                                         double* thr, int* pol, double* alpha, int rec_len,
                                         float* rec_f, double* rec_d, int* fitted);
+__global__ void logitboost_cluster_kernel(const DevModel* M, int m, int J, const double* X,
+                                          const int* label, int n_rounds, double* sorted_v,
+                                          int* sorted_i, int max_stumps, int* n_stumps, int* feat,
+                                          double* thr, int* pol, double* alpha, int rec_len,
+                                          float* rec_f, double* rec_d, int* fitted);
 __global__ void newton_decide_kernel(IterState* s, const int* count, int max_iter,
                                      cudaGraphConditionalHandle h, int* passes);
 __global__ void set_int_kernel(int* p, int v);

@@ -119,3 +119,56 @@ def test_sampler_argument_checks():
         opt.fit_classifier(CMCParams(J=16, N2=64, n_stumps=4, seed=1, sampler=2))
     assert e.value.status == bap.BAP_EINVAL
     opt.close()
+
+
+def test_logitboost_matches_the_oracle_on_gpu_labels():
+    """LogitBoost on the cluster: per date, the oracle's LogitBoost on the GPU's own training
+    points and labels gives the same rounds (two vote stumps each)."""
+    spec = spec_basket_put_7(0)
+    params = CMCParams(J=600, N2=800, n_stumps=30, seed=11, boost=1)
+    opt = bap.Option(spec)
+    opt.fit_classifier(params)
+    quad, nst = _stumps(opt, spec)
+    for m in range(1, spec.n_dates):
+        y, _, _ = opt.fit_points(m)
+        X = oracle.train_points(spec, m, params.J, params.seed)
+        Fx = np.concatenate([X, oracle.payoff(spec, X)[:, None]], axis=1)
+        st = oracle.logit_to_stumps(oracle.logitboost(Fx, np.where(y > 0, 1, -1), params.n_stumps))
+        assert nst[m] == len(st), m
+        for i, (f, thr, pol, al) in enumerate(st):
+            gf, gt, gp, ga = quad[m, i]
+            assert int(gf) == f, (m, i)
+            assert (math.isinf(thr) and math.isinf(gt)) or abs(gt - thr) <= 1e-9 * max(1, abs(thr))
+            if al > 1e-9:
+                assert int(gp) == pol, (m, i)
+            assert abs(ga - al) <= 1e-8 * max(1.0, abs(al)), (m, i, ga, al)
+    opt.close()
+
+
+def test_logitboost_cmc_fit_and_price_match_the_oracle():
+    spec = spec_max_call(3, 100.0, rho=0.0, n_dates=6, T=2.0)
+    params = CMCParams(J=800, N2=600, n_stumps=40, seed=4, boost=1)
+    opt = bap.Option(spec)
+    opt.fit_classifier(params)
+    o_rules, o_diag = oracle.cmc_fit(spec, params, n_threads=8)
+    agree = total = 0
+    for m, dg in o_diag.items():
+        y, _, _ = opt.fit_points(m)
+        agree += int(np.sum(np.sign(y) == np.sign(dg["y"])))
+        total += len(y)
+    assert agree >= total - 3
+    g = opt.price(200_000, 6)
+    o = oracle.price(spec, o_rules, 200_000, 6, n_threads=8)
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"], (g, o)
+    opt.close()
+
+
+def test_logitboost_argument_checks():
+    opt = bap.Option(spec_put_1d(n_dates=3))
+    for bad in (CMCParams(J=16, N2=64, n_stumps=4, seed=1, boost=2),
+                CMCParams(J=5000, N2=64, n_stumps=4, seed=1, boost=1),
+                CMCParams(J=16, N2=64, n_stumps=200, seed=1, boost=1)):
+        with pytest.raises(bap.BapError) as e:
+            opt.fit_classifier(bad)
+        assert e.value.status == bap.BAP_EINVAL
+    opt.close()
