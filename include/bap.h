@@ -185,6 +185,17 @@ bap_status bap_set_launch_mode(bap_option *opt, int mode);
  * Errors: EINVAL (null option). */
 bap_status bap_set_wait_limit(bap_option *opt, uint64_t ns);
 
+/* Bounds checks of the checked build (the library compiled with -DBAP_CHECKS, a debug aid in
+ * place of a sanitizer): the path kernel checks its item, list, slot, rule-row and trace
+ * indices, skips an access that fails and counts it.  *count = failures since the option got its
+ * model, *first_code = the first failure's check (1 item, 2 list position, 3 trace index,
+ * 4 unit slot, 5 rule row; 0 none).  Always 0 in the normal build.  Waits for the option's
+ * stream.  Errors: EINVAL (null argument), ECUDA. */
+bap_status bap_debug_checks(bap_option *opt, uint64_t *count, int *first_code);
+
+/* 1 in the checked build, 0 in the normal one. */
+int bap_checked_build(void);
+
 /* How bap_fit_classifier runs the boosting of each date ([class], Section 3.2; the paper's
  * sequential bottleneck).  1 (default): a thread-block cluster of d+1 blocks, one per feature,
  * each sorting and scanning its feature while the blocks exchange per-round minima through

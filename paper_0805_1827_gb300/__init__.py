@@ -24,6 +24,7 @@ MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
 EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
             "bap_set_boost_form", "bap_last_boost_form", "bap_set_wait_limit",
+            "bap_debug_checks", "bap_checked_build",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
             "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
@@ -89,14 +90,16 @@ _lib = None
 
 
 def lib():
-    """The loaded libbap.so (built on first use if the CUDA toolkit is present)."""
+    """The loaded libbap.so (built on first use if the CUDA toolkit is present).  BAP_LIB names
+    another build of the same library to load instead (the bounds-checked debug build)."""
     global _lib
     if _lib is None:
-        if needs_build():
+        path = os.environ.get("BAP_LIB") or _LIB_PATH
+        if path == _LIB_PATH and needs_build():
             build()
-        if not os.path.exists(_LIB_PATH):
-            raise ImportError(f"libbap.so not found at {_LIB_PATH}; run paper_0805_1827_gb300.build()")
-        L = C.CDLL(_LIB_PATH)
+        if not os.path.exists(path):
+            raise ImportError(f"libbap.so not found at {path}; run paper_0805_1827_gb300.build()")
+        L = C.CDLL(path)
         vp = C.c_void_p
         dp, ip, i64p = C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int64)
         L.bap_create.argtypes = [C.POINTER(_Model), C.POINTER(vp)]
@@ -105,6 +108,8 @@ def lib():
         L.bap_set_launch_mode.argtypes = [vp, C.c_int]
         L.bap_set_boost_form.argtypes = [vp, C.c_int]
         L.bap_set_wait_limit.argtypes = [vp, C.c_uint64]
+        L.bap_debug_checks.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]
+        L.bap_checked_build.argtypes = []
         L.bap_last_boost_form.argtypes = [vp, C.POINTER(C.c_int)]
         L.bap_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(vp)]
         L.bap_server_set_launch_mode.argtypes = [vp, C.c_int]
@@ -208,6 +213,12 @@ class Option:
 
     def set_launch_mode(self, mode: int):
         _check(lib().bap_set_launch_mode(self.h, mode))
+
+    def debug_checks(self):
+        """(failed bounds checks, first failing check) of the checked build; (0, 0) otherwise."""
+        n, first = C.c_uint64(0), C.c_int(0)
+        _check(lib().bap_debug_checks(self.h, C.byref(n), C.byref(first)))
+        return n.value, first.value
 
     def set_wait_limit(self, ns: int):
         _check(lib().bap_set_wait_limit(self.h, ns))

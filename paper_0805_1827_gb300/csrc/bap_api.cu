@@ -263,6 +263,8 @@ void phase_collect(bap_option* o) {
 void base_args(bap_option* o, PathArgs& a, int m, int mode, bool fp64) {
     memset(&a, 0, sizeof a);
     a.model = o->dmodel.as<DevModel>();
+    a.n_items = o->n_items;
+    a.checks = o->check_buf.as<unsigned long long>();
     a.m = m;
     a.mode = mode;
     a.n_dates = o->n_dates;
@@ -600,6 +602,7 @@ bap_status run_sums_enqueue(bap_option* o, int m, int mode, bool fp64, const Rou
     ++o->launches;
     PathArgs a;
     base_args(o, a, m, mode, fp64);
+    a.n_items = n_items;
     a.rk = rk;
     a.N = N;
     a.chunk = chunk;
@@ -819,6 +822,8 @@ bap_status option_load(bap_option* o, const DevModel& hm) {
     TRY(o->total_steps.reserve(8));
     TRY(o->stat_counts.reserve(16));
     TRY(o->one.reserve(8));
+    TRY(o->check_buf.reserve(16));
+    CU(cudaMemsetAsync(o->check_buf.p, 0, 16, o->stream));
     CU(cudaMemcpyAsync(o->dmodel.p, &o->hm, sizeof(DevModel), cudaMemcpyHostToDevice, o->stream));
     CU(cudaMemcpyAsync(o->s0buf.p, o->hm.S0, (size_t)hm.d * 8, cudaMemcpyHostToDevice, o->stream));
     CU(cudaMemsetAsync(o->fitted.p, 0, (hm.n_dates + 1) * sizeof(int), o->stream));
@@ -1284,6 +1289,24 @@ bap_status bap_set_launch_mode(bap_option* o, int mode) {
     return BAP_OK;
 }
 
+bap_status bap_debug_checks(bap_option* o, uint64_t* count, int* first_code) {
+    if (!o || !count || !first_code) return fail(BAP_EINVAL, "null argument");
+    unsigned long long h[2] = {0, 0};
+    CU(cudaMemcpyAsync(h, o->check_buf.p, 16, cudaMemcpyDeviceToHost, o->stream));
+    CU(cudaStreamSynchronize(o->stream));
+    *count = h[0];
+    *first_code = (int)h[1];
+    return BAP_OK;
+}
+
+int bap_checked_build(void) {
+#ifdef BAP_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 bap_status bap_set_wait_limit(bap_option* o, uint64_t ns) {
     if (!o) return fail(BAP_EINVAL, "null option");
     o->wait_limit_ns = ns;
@@ -1616,6 +1639,7 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
 
     PathArgs a;
     base_args(o, a, m, MODE_SUMS, false);
+    a.n_items = n_items;
     a.rk = make_round_keys(seed, (uint32_t)purpose, (uint32_t)m);
     a.N = N;
     a.chunk = chunk;

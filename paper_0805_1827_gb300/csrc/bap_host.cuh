@@ -121,7 +121,7 @@ struct bap_option {
     bap::DevBuf start, state, pivot, ctr_item, active0, active1, counts, work, partial,
         partial_steps, done, total_steps, korobov_a, merit, label_y, label, sorted_v, sorted_i,
         err, out_sums, out_steps, out_sums64, out_steps64, trace_tau, trace_phi, diag_x, diag_it,
-        diag_st, stat_counts, one, iterstate, bridge_w;
+        diag_st, stat_counts, one, iterstate, bridge_w, check_buf;
     int last_noconv = 0, last_noroot = 0;
     long long last_fit_steps = 0;
     double last_fit_ms = 0;
@@ -159,7 +159,8 @@ struct bap_option {
                               &partial_steps, &done, &total_steps, &korobov_a, &merit, &label_y,
                               &label, &sorted_v, &sorted_i, &err, &out_sums, &out_steps,
                               &out_sums64, &out_steps64, &trace_tau, &trace_phi, &diag_x,
-                              &diag_it, &diag_st, &stat_counts, &one, &iterstate, &bridge_w};
+                              &diag_it, &diag_st, &stat_counts, &one, &iterstate, &bridge_w,
+                              &check_buf};
         for (bap::DevBuf* b : all) f(*b);
     }
 };

@@ -20,6 +20,22 @@ constexpr int WARP = 32;
 
 enum Purpose : uint32_t { P_IZ = 1, P_CMC = 2, P_TRAIN = 3, P_PRICE = 4 };
 enum RuleKind : int { R_NONE = 0, R_IZ = 1, R_CMC = 2 };
+// Bounds checks of the checked build (compiled with -DBAP_CHECKS, a debug aid in place of a
+// sanitizer): bap_check(cond, code, buf) counts a failed condition in buf[0], keeps the first
+// code in buf[1] and returns false so that the caller skips the access.  In the normal build it
+// is the constant true and costs nothing.
+#ifdef BAP_CHECKS
+__device__ __forceinline__ bool bap_check(bool cond, int code, unsigned long long* buf) {
+    if (!cond && buf) {
+        atomicAdd(buf, 1ULL);
+        atomicCAS(buf + 1, 0ULL, (unsigned long long)code);
+    }
+    return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool bap_check(bool, int, unsigned long long*) { return true; }
+#endif
+
 // Kernel selectors (not rule kinds): the cooperative kernel that runs all Newton passes of a date,
 // and the I&Z kernels for cubic boundaries (one pass, cooperative).
 constexpr int R_NEWTON_COOP = 3;

@@ -71,6 +71,8 @@ struct PathArgs {
     unsigned long long coop_limit_ns;
     double f_tol, x_tol, fp_eps;
     int max_iter, fixed_point;
+    int n_items;                 // items the buffers hold (list capacity; bounds checks)
+    unsigned long long* checks;  // bounds-check counters of the checked build (or nullptr)
     double* label_y;             // MODE_LABEL: Phi - C
     int* label;                  // +1 exercise / -1 continue
 };
@@ -361,6 +363,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             const int chunk = (int)(unit - (long long)slot * a.C);
             const int* active = a.list[it & 1];
             const int item = active ? __ldcg(active + slot) : slot;
+            if (!bap_check(item >= 0 && item < a.n_items, 1, a.checks)) continue;
 
             // log2 of the start point in FP64, one coordinate per lane, then broadcast
             const double* st = a.start + (size_t)item * D;
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                     bool ex = phi > 0;
                     if (ex && k < a.n_dates) {
                         const int kr = k - a.m - 1;
+                        bap_check(kr >= 0 && kr < a.n_dates - a.m - 1, 5, a.checks);
                         if (RULE == R_NONE || !sh_fit[kr]) {
                             ex = false;
                         } else if (RULE == R_IZ) {
@@ -559,8 +563,10 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                             }
                         }
                         if (a.mode == MODE_TRACE) {
-                            a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
-                            a.trace_phi[n_begin + nl] = (double)v;
+                            if (bap_check(n_begin + nl < a.N, 3, a.checks)) {
+                                a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
+                                a.trace_phi[n_begin + nl] = (double)v;
+                            }
                         }
                         acc0 += v;
                         acc1 += v * v;
@@ -593,6 +599,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             int last = 0;
             if (lane == 0) {
                 const size_t o = (size_t)item * a.C + chunk;
+                bap_check(chunk >= 0 && chunk < a.C, 4, a.checks);
                 a.partial[3 * o + 0] = s0;
                 a.partial[3 * o + 1] = s1;
                 a.partial[3 * o + 2] = s2;
@@ -637,7 +644,8 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                     const double x = __ldcg(&a.state[item].x);
                     if (newton_update(a, item, t0 / Nd, t2 / (Nd * x))) {
                         const int pos = atomicAdd(a.count + it + 1, 1);
-                        a.list[(it + 1) & 1][pos] = item;
+                        if (bap_check(pos >= 0 && pos < a.n_items, 2, a.checks))
+                            a.list[(it + 1) & 1][pos] = item;
                     }
                 } else if (a.mode == MODE_LABEL) {
                     const double phi = payoff64(a, a.start + (size_t)item * D, D);
