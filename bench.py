@@ -28,6 +28,8 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# before any CUDA context exists: hardware queues for the serving loop's per-request streams
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from bap_workloads import IZParams, serving_stream, spec_max_call  # noqa: E402
 

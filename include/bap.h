@@ -286,7 +286,11 @@ bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_
  * same calls made alone through bap_create / bap_fit_* / bap_price.  All server calls are
  * thread safe.  The server uses the device current at bap_server_create. */
 
-/* Errors: EINVAL (budget < 1 MiB, max_inflight outside 1..1024), ECUDA (no device), ENOMEM. */
+/* Errors: EINVAL (budget < 1 MiB, max_inflight outside 1..1024), ECUDA (no device), ENOMEM.
+ * Each request in flight runs on its own stream: set CUDA_DEVICE_MAX_CONNECTIONS=32 in the
+ * environment before the process creates its CUDA context, else CUDA multiplexes the streams
+ * onto 8 hardware queues and requests wait for each other (the Python binding sets it at
+ * import unless it is already set). */
 bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_server **out);
 
 /* Launch form of the I&Z fits the server runs (see bap_set_launch_mode).  Default 2 (one
