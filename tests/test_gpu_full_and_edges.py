@@ -182,3 +182,51 @@ def test_bad_arguments_are_rejected():
                               rho=[[1.0, 1.0], [1.0, 1.0]], r=0.05, K=100.0, T=1.0, n_dates=2))
     assert e.value.status == bap.BAP_EINVAL   # not positive definite
     opt.close()
+
+
+# ---- edges of the method variants ------------------------------------------------------------
+
+def test_cubic_boundary_at_the_largest_d():
+    """d = 6: the cubic in 5 variables has 56 coefficients (the most the fit holds)."""
+    from test_gpu_parity import _iz_fit_compare
+    spec = spec_max_call(6, 100.0, rho=0.2, n_dates=4, T=1.0)
+    _iz_fit_compare(spec, IZParams(J=128, N1=4000, degree=3, seed=3), 100_000, 2)
+
+
+def test_logitboost_on_an_eleven_block_cluster_and_at_its_largest_J():
+    for spec, J in ((spec_max_call(10, 100.0, rho=0.3, n_dates=3, T=1.0), 300),
+                    (spec_put_1d(n_dates=3), 4096)):
+        params = CMCParams(J=J, N2=200, n_stumps=8, seed=5, boost=1)
+        opt = bap.Option(spec)
+        opt.fit_classifier(params)
+        assert opt.last_boost_form() == 1
+        m = spec.n_dates - 1
+        y, _, _ = opt.fit_points(m)
+        X = oracle.train_points(spec, m, J, params.seed)
+        Fx = np.concatenate([X, oracle.payoff(spec, X)[:, None]], axis=1)
+        st = oracle.logit_to_stumps(oracle.logitboost(Fx, np.where(y > 0, 1, -1), params.n_stumps))
+        buf = opt.export_rules()
+        nd = spec.n_dates + 1
+        ms = int(buf[5])
+        quad = buf[6 + nd: 6 + nd + nd * ms * 4].reshape(nd, ms, 4)
+        for i, (f, thr, pol, al) in enumerate(st):
+            assert int(quad[m, i, 0]) == f, (spec.d, i)
+            assert abs(quad[m, i, 3] - al) <= 1e-8 * max(1.0, al), (spec.d, i)
+        r = opt.price(50_000, 3)
+        assert r["price"] > 0 and abs(r["fp64_delta"]) < 0.2 * r["se"]
+        opt.close()
+
+
+def test_bridge_sampler_in_one_dimension():
+    spec = spec_put_1d(n_dates=8)
+    params = CMCParams(J=300, N2=500, n_stumps=20, seed=6, sampler=1)
+    opt = bap.Option(spec)
+    opt.fit_classifier(params)
+    o_rules, o_diag = oracle.cmc_fit(spec, params, n_threads=8)
+    for m, dg in o_diag.items():
+        y, _, _ = opt.fit_points(m)
+        assert np.mean(np.abs(y - dg["y"]) <= 1e-4 * np.maximum(1.0, np.abs(dg["y"])) + 2e-4) >= 0.97
+    g = opt.price(100_000, 4)
+    o = oracle.price(spec, o_rules, 100_000, 4, n_threads=8)
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"]
+    opt.close()

@@ -171,3 +171,29 @@ def test_phase_timers_cover_the_fit():
     glp, calc, cls, mc = r["phase_ms"]
     assert glp == 0 and calc > 0 and cls > 0
     o.close()
+
+
+def test_served_method_variants_equal_results_alone():
+    """Cubic boundaries, LogitBoost and the bridge sampler through the serving loop: bitwise the
+    results of the same requests run alone."""
+    reqs = [
+        (spec_max_call(3, 100.0, rho=0.2, n_dates=5, T=1.5), IZParams(J=64, N1=4000, degree=3, seed=1)),
+        (spec_max_call(4, 95.0, rho=0.3, n_dates=6, T=2.0), CMCParams(J=500, N2=400, n_stumps=12, seed=2, boost=1)),
+        (spec_put_1d(n_dates=7), CMCParams(J=400, N2=500, n_stumps=20, seed=3, sampler=1)),
+        (spec_max_call(2, 110.0, rho=0.0, n_dates=4, T=1.0), IZParams(J=32, N1=3000, degree=1, seed=4,
+                                                                        fixed_point=1, fp_eps=0.01)),
+    ]
+    srv = bap.Server(device_mem_budget=4 << 30, max_inflight=4)
+    tickets = [srv.submit(s, p, 50_000, 9) for s, p in reqs]
+    served = [srv.wait(t, 300.0) for t in tickets]
+    srv.close()
+    for (spec, params), (st, res) in zip(reqs, served):
+        o = bap.Option(spec)
+        o.set_launch_mode(bap.LAUNCH_COOP)
+        if isinstance(params, IZParams):
+            o.fit_boundary(params)
+        else:
+            o.fit_classifier(params)
+        alone = o.price(50_000, 9)
+        o.close()
+        assert res["price"] == alone["price"] and res["var"] == alone["var"], params
