@@ -79,6 +79,7 @@ class IZParams:
     seed: int = 0
     fixed_point: int = 0      # 1: the literal fixed-point iteration with tolerance fp_eps
     fp_eps: float = 0.01
+    warm_start: int = 0       # 1: start each point at the later date's fitted boundary value
 
 
 @dataclass

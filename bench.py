@@ -401,16 +401,18 @@ def paper_tables(bap) -> dict:
 
 
 def root_find_study(bap) -> dict:
-    """Safeguarded Newton against the paper's literal fixed-point iteration (eps = 0.01) on the
+    """Safeguarded Newton (from the bracket edge, and warm-started at the later date's fitted
+    boundary) against the paper's literal fixed-point iteration (eps = 0.01) on the
     Table 1 workload (3-asset max-call, S0=90, J=128, N1=5e3, 8 fitted dates, max_iter 100):
     continuation evaluations per boundary point (mean, median, p90, max: the load imbalance
     among points), points without convergence, inner path-steps, fit time and price."""
     import numpy as np
     out = {}
-    for name, fp in (("newton", 0), ("fixed_point", 1)):
+    for name, fp, warm in (("newton", 0, 0), ("newton_warm_start", 0, 1), ("fixed_point", 1, 0)):
         spec = spec_max_call(3, 90.0)
         o = bap.Option(spec)
-        p = IZParams(J=128, N1=5000, degree=2, seed=1, fixed_point=fp, fp_eps=0.01, max_iter=100)
+        p = IZParams(J=128, N1=5000, degree=2, seed=1, fixed_point=fp, fp_eps=0.01, max_iter=100,
+                     warm_start=warm)
         o.fit_boundary(p)
         r = o.price(1_000_000, 2)
         its = np.concatenate([o.fit_points(m)[1] for m in range(1, spec.n_dates)])

@@ -93,6 +93,11 @@ typedef struct bap_iz_params {
     int fixed_point;          /* 1: the paper's literal iteration x <- Phi^-1(C(x)) with |dx| <
                                  fp_eps (Section 2.4); 0: safeguarded Newton */
     double fp_eps;
+    int warm_start;           /* 1: each boundary point starts at the later date's fitted boundary
+                                 value K B_{m+1}(S_{-p}/K) when that lies inside its initial
+                                 bracket (the paper's "approximate points" refined by Newton);
+                                 0: at the edge of the bracket (max(K, max S_{-p}) for the
+                                 max-call); same results to the convergence tolerances */
 } bap_iz_params;
 
 /* Picazo CMC parameters (Section 3.2-3.3, Algorithm 2). */

@@ -106,7 +106,7 @@ def _lib(precision: str = "f64"):
             lib.orc_newton.argtypes = [mp, rp, C.c_int, C.c_int, C.c_uint64, C.c_int,
                                        C.POINTER(C.c_int), C.POINTER(C.c_int),
                                        C.POINTER(C.c_double), C.c_int64, C.c_double, C.c_double,
-                                       C.c_int, C.c_int, C.c_double, C.c_int,
+                                       C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
                                        C.POINTER(C.c_double), C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), i64p]
             lib.orc_price.argtypes = [mp, rp, C.c_int, C.c_uint64, C.c_int64, C.c_int,
@@ -498,7 +498,8 @@ def newton_points(spec: OptionSpec, rules: Rules, m: int, params: IZParams, ids,
     steps = np.zeros(n, dtype=np.int64)
     rc = lib.orc_newton(C.byref(M.c), C.byref(R), m, PURPOSE_IZ, params.seed, n, _ip(ids),
                         _ip(piv), _dp(starts), params.N1, params.f_tol, params.x_tol,
-                        params.max_iter, params.fixed_point, params.fp_eps, n_threads, _dp(x),
+                        params.max_iter, params.fixed_point, params.fp_eps,
+                        getattr(params, "warm_start", 0), n_threads, _dp(x),
                         _ip(it), _ip(st), steps.ctypes.data_as(C.POINTER(C.c_int64)))
     if rc:
         raise ValueError("orc_newton rejected its arguments")

@@ -360,9 +360,24 @@ static double payoff_at(const orc_model *M, const double *start)
     return payoff(M, S);
 }
 
+/* I&Z boundary of date k for boundary p at the other assets of S: K B_k(S_{-p}/K) (FP64, the
+ * fitted coefficients in basis order). */
+static double boundary_value(const orc_model *M, const orc_rule *R, int k, int p, const double *S)
+{
+    double y[ORC_MAXD], ph[ORC_MAXBASIS];
+    int s = 0;
+    for (int q = 0; q < M->d; ++q) if (q != p) y[s++] = S[q] / M->K;
+    int nb = basis(s, R->degree, y, ph);
+    const double *c = R->coef + ((size_t)k * R->n_bnd + (R->n_bnd > 1 ? p : 0)) * R->n_coef;
+    double B = 0;
+    for (int i = 0; i < nb; ++i) B += c[i] * ph[i];
+    return M->K * B;
+}
+
 static void newton_item(const orc_model *M, const orc_rule *R, int m, const uint32_t key[2],
                         uint32_t item, int p, const double *start_in, int64_t N,
                         double f_tol, double x_tol, int max_iter, int fixed_point, double fp_eps,
+                        int warm_start,
                         double *x_out, int *iters_out, int *status_out, int64_t *steps_out)
 {
     int d = M->d;
@@ -391,6 +406,12 @@ static void newton_item(const orc_model *M, const orc_rule *R, int m, const uint
             return;
         }
         lo = 0; hi = top; x = top * (1.0 - 1e-3);
+    }
+    /* warm start: the later date's fitted boundary at these other assets, when it lies inside
+     * the initial bracket (the boundary moves little from one date to the next) */
+    if (warm_start && R->kind == RULE_IZ && m + 1 < M->n_dates && R->fitted[m + 1]) {
+        double xw = boundary_value(M, R, m + 1, p, start_in);
+        if (xw > lo && xw < hi) x = xw;
     }
     double x_max = 1e3 * K, x_min = 1e-6 * K;
     double dx_old = INFINITY, dx = INFINITY;
@@ -457,7 +478,8 @@ static void newton_item(const orc_model *M, const orc_rule *R, int m, const uint
 int orc_newton(const orc_model *M, const orc_rule *R, int m, int purpose, uint64_t seed,
                int n_items, const int *item_id, const int *pivot, const double *start, int64_t N,
                double f_tol, double x_tol, int max_iter, int fixed_point, double fp_eps,
-               int n_threads, double *x_out, int *iters, int *status, int64_t *steps)
+               int warm_start, int n_threads, double *x_out, int *iters, int *status,
+               int64_t *steps)
 {
     if (M->d < 1 || M->d > ORC_MAXD || m < 0 || m >= M->n_dates) return 1;
     uint32_t key[2];
@@ -468,8 +490,8 @@ int orc_newton(const orc_model *M, const orc_rule *R, int m, int purpose, uint64
 #endif
     for (int i = 0; i < n_items; ++i)
         newton_item(M, R, m, key, (uint32_t)item_id[i], pivot[i], start + (size_t)i * M->d, N,
-                    f_tol, x_tol, max_iter, fixed_point, fp_eps, x_out + i, iters + i, status + i,
-                    steps + i);
+                    f_tol, x_tol, max_iter, fixed_point, fp_eps, warm_start, x_out + i, iters + i,
+                    status + i, steps + i);
     return 0;
 }
 

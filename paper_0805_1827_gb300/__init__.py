@@ -58,7 +58,7 @@ class _Model(C.Structure):
 class _IZ(C.Structure):
     _fields_ = [("J", C.c_int), ("N1", C.c_int64), ("f_tol", C.c_double), ("x_tol", C.c_double),
                 ("max_iter", C.c_int), ("degree", C.c_int), ("seed", C.c_uint64),
-                ("fixed_point", C.c_int), ("fp_eps", C.c_double)]
+                ("fixed_point", C.c_int), ("fp_eps", C.c_double), ("warm_start", C.c_int)]
 
 
 class _CMC(C.Structure):
@@ -183,7 +183,7 @@ def _model(spec):
 def _params(p):
     if hasattr(p, "N1"):
         return 0, _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point,
-                      p.fp_eps)
+                      p.fp_eps, getattr(p, "warm_start", 0))
     return 1, _CMC(p.J, p.N2, p.n_stumps, p.seed, getattr(p, "sampler", 0), getattr(p, "boost", 0))
 
 
@@ -238,7 +238,8 @@ class Option:
         return v.value
 
     def fit_boundary(self, p) -> int:
-        c = _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point, p.fp_eps)
+        c = _IZ(p.J, p.N1, p.f_tol, p.x_tol, p.max_iter, p.degree, p.seed, p.fixed_point, p.fp_eps,
+                getattr(p, "warm_start", 0))
         return _check(lib().bap_fit_boundary(self.h, C.byref(c)), (BAP_OK, BAP_ENOCONV))
 
     def fit_classifier(self, p) -> int:

@@ -480,7 +480,8 @@ bap_status enqueue_iz_setup(bap_option* o, const bap_iz_params* p, int m, bool d
     int* count0 = o->counts.as<int>();
     iz_setup_kernel<<<(o->n_items + 127) / 128, 128, 0, st>>>(
         o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
-        o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), count0);
+        o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), count0,
+        o->coef64.as<double>(), o->n_coef, o->degree, o->fitted.as<int>(), p->warm_start);
     ++o->launches;
     CU(cudaGetLastError());
     return BAP_OK;
@@ -581,7 +582,7 @@ bap_status build_iz_graph(bap_option* o, const bap_iz_params* p, int chunk, int 
 bool same_iz(const bap_iz_params& a, const bap_iz_params& b) {
     return a.J == b.J && a.N1 == b.N1 && a.f_tol == b.f_tol && a.x_tol == b.x_tol &&
            a.max_iter == b.max_iter && a.degree == b.degree && a.seed == b.seed &&
-           a.fixed_point == b.fixed_point && a.fp_eps == b.fp_eps;
+           a.fixed_point == b.fixed_point && a.fp_eps == b.fp_eps && a.warm_start == b.warm_start;
 }
 
 bap_status run_sums_enqueue(bap_option* o, int m, int mode, bool fp64, const RoundKeys& rk,
@@ -873,6 +874,7 @@ bap_status validate_iz(int d, const bap_iz_params* p) {
         return fail(BAP_EINVAL, "cubic boundaries need d <= %d", MAXD_CUBIC);
     if (!(p->f_tol >= 0) || !(p->x_tol >= 0)) return fail(BAP_EINVAL, "negative tolerance");
     if (p->fixed_point && !(p->fp_eps > 0)) return fail(BAP_EINVAL, "fp_eps must be positive");
+    if (p->warm_start != 0 && p->warm_start != 1) return fail(BAP_EINVAL, "warm_start outside 0..1");
     return BAP_OK;
 }
 

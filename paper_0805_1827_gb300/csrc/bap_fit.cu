@@ -85,7 +85,8 @@ __global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_
 
 __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
                                 double* start, ItemState* state, int* pivot, int* active,
-                                int* count) {
+                                int* count, const double* coef64, int n_coef, int degree,
+                                const int* fitted, int warm_start) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= n_bnd * J) return;
     const int d = M->d, s = d - 1;
@@ -105,7 +106,6 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
         g = (g * a) % (unsigned long long)J;
         ++c;
     }
-    (void)s;
     ItemState st;
     st.iters = 0;
     st.status = ST_OK;
@@ -145,6 +145,29 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
             st.hi = top;
             st.x = top * (1.0 - 1e-3);
         }
+    }
+    // warm start: the later date's fitted boundary K B_{m+1}(S_{-p}/K) (FP64, basis order
+    // [1, y_a, y_a y_b, y_a y_b y_c]) when it lies inside the initial bracket
+    if (live && warm_start && m + 1 < M->n_dates && fitted[m + 1]) {
+        double y[MAXD];
+        int t = 0;
+        for (int q = 0; q < d; ++q)
+            if (q != p) y[t++] = S[q] / K;
+        const double* c = coef64 + ((size_t)(m + 1) * n_bnd + b) * n_coef;
+        double B = 0.0;
+        int i = 0;
+        B += c[i++] * 1.0;
+        if (degree >= 1)
+            for (int a = 0; a < s; ++a) B += c[i++] * y[a];
+        if (degree >= 2)
+            for (int a = 0; a < s; ++a)
+                for (int e = a; e < s; ++e) B += c[i++] * (y[a] * y[e]);
+        if (degree >= 3)
+            for (int a = 0; a < s; ++a)
+                for (int e = a; e < s; ++e)
+                    for (int g3 = e; g3 < s; ++g3) B += c[i++] * (y[a] * y[e] * y[g3]);
+        const double xw = K * B;
+        if (xw > st.lo && xw < st.hi) st.x = xw;
     }
     S[p] = st.x;
     state[item] = st;

@@ -9,7 +9,8 @@ __global__ void korobov_merit_kernel(int J, int s, double* merit);
 __global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_a);
 __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
                                 double* start, ItemState* state, int* pivot, int* active,
-                                int* count);
+                                int* count, const double* coef64, int n_coef, int degree,
+                                const int* fitted, int warm_start);
 __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
                                 int degree, double K, float* coef_f, double* coef_d);
 // Threads per block of ls_fit_kernel (one block per boundary).

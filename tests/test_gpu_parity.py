@@ -274,3 +274,12 @@ def test_cubic_rules_round_trip():
     assert ra["price"] == rb["price"] and ra["var"] == rb["var"]
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("d", [3, 5])
+def test_fit_with_warm_started_newton(d):
+    """Warm-started Newton (each point from the later date's fitted boundary) against the
+    oracle's, at the points and the price."""
+    spec = spec_max_call(d, 100.0, rho=0.2, n_dates=5, T=1.5)
+    params = IZParams(J=64, N1=8000, degree=2, seed=3, warm_start=1)
+    _iz_fit_compare(spec, params, 100_000, 4)

@@ -116,3 +116,21 @@ def test_symmetric_under_permuting_iid_assets():
         out.append(oracle.price(spec, rules, 300_000, seed=8, n_threads=4))
     tol = 4 * math.hypot(pa[0]["se"], pb[0]["se"])
     assert abs(pa[0]["price"] - pb[0]["price"]) < tol
+
+
+def test_warm_started_newton_needs_fewer_evaluations_and_prices_the_same():
+    """Starting each boundary point at the later date's fitted boundary (warm start) converges
+    to the same points within the tolerances, in fewer continuation evaluations."""
+    from bap_workloads import IZParams
+    spec = spec_max_call(3, 90.0, n_dates=5, T=1.5)
+    res = {}
+    for warm in (0, 1):
+        rules, diag = oracle.iz_fit(spec, IZParams(J=32, N1=4000, degree=2, seed=1,
+                                                   warm_start=warm), n_threads=8)
+        its = np.concatenate([np.asarray(d["iters"]) for d in diag.values()])
+        res[warm] = (rules, diag, its, oracle.price(spec, rules, 100_000, seed=2, n_threads=8))
+    (_, d0, it0, p0), (_, d1, it1, p1) = res[0], res[1]
+    last = max(d0)
+    assert np.array_equal(it0[: len(d0[last]["iters"])], it1[: len(d1[last]["iters"])])  # no later date
+    assert it1.mean() < it0.mean()
+    assert abs(p0["price"] - p1["price"]) < 3 * np.hypot(p0["se"], p1["se"])
