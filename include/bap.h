@@ -201,15 +201,19 @@ bap_status bap_debug_checks(bap_option *opt, uint64_t *count, int *first_code);
 /* 1 in the checked build, 0 in the normal one. */
 int bap_checked_build(void);
 
-/* How bap_fit_classifier runs the boosting of each date ([class], Section 3.2; the paper's
- * sequential bottleneck).  1 (default): a thread-block cluster of d+1 blocks, one per feature,
- * each sorting and scanning its feature while the blocks exchange per-round minima through
- * distributed shared memory; used when the device can place such a cluster, else the one-block
- * form.  0: one 1024-thread block for all features.  Both pick the stumps by the same rule on
- * exact fixed-point errors.  Errors: EINVAL (null option, form outside 0..1). */
+/* How bap_fit_classifier runs the AdaBoost of each date ([class], Section 3.2; the paper's
+ * sequential bottleneck).  3 (default): form 2 for J <= 2048, form 1 above.  2: one 512-thread
+ * block with one warp per feature, the sorted orders and weights held in shared memory; used when
+ * they fit (J <= 4096 for d = 10), else form 1.  1: a thread-block cluster of d+1 blocks, one per
+ * feature, exchanging per-round minima through distributed shared memory; used when the device
+ * can place such a cluster, else form 0.  0: one 1024-thread block for all features.  All forms
+ * pick the stumps by the same rule on exact fixed-point errors and update the weights by the
+ * closed form of the normalised update, so they give identical stumps bit for bit.  LogitBoost
+ * (bap_cmc_params.boost = 1) always runs on the cluster.
+ * Errors: EINVAL (null option, form outside 0..3). */
 bap_status bap_set_boost_form(bap_option *opt, int form);
 
-/* The form the last bap_fit_classifier ran (*form = 1 cluster, 0 one block).
+/* The form the last bap_fit_classifier ran (*form = 2 warp per feature, 1 cluster, 0 one block).
  * Errors: EINVAL (null argument). */
 bap_status bap_last_boost_form(const bap_option *opt, int *form);
 

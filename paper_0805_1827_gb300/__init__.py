@@ -37,7 +37,7 @@ EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch
             "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait", "bap_cancel",
             "bap_server_get_stats", "bap_server_destroy"]
 LAUNCH_PLAIN, LAUNCH_GRAPH, LAUNCH_COOP = 0, 1, 2
-BOOST_ONE_BLOCK, BOOST_CLUSTER = 0, 1
+BOOST_ONE_BLOCK, BOOST_CLUSTER, BOOST_WARP, BOOST_AUTO = 0, 1, 2, 3
 METHOD_CODE = {"iz": 0, "cmc": 1}
 
 

@@ -88,6 +88,8 @@ constexpr int kBlock = 256;
 // occupancy for the last shared-memory size asked about.
 struct FnInfo {
     bool smem_raised = false;
+    size_t max_dyn_smem = 0;          // the raised limit
+
     size_t occ_smem = ~size_t(0);
     int occ_blocks = 0;
 };
@@ -104,6 +106,7 @@ bap_status raise_smem_limit(const void* fn, int device, FnInfo& fi) {
     cudaFuncAttributes fa;
     CU(cudaFuncGetAttributes(&fa, fn));
     CU(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    fi.max_dyn_smem = (size_t)(optin - (int)fa.sharedSizeBytes);
     fi.smem_raised = true;
     return BAP_OK;
 }
@@ -738,8 +741,8 @@ bap_status preload_kernels(int device) {
                 }
             }
         }
-        const void* ab = (const void*)adaboost_kernel;
-        TRY(raise_smem_limit(ab, device, g_fn[{ab, device}]));
+        for (const void* ab : {(const void*)adaboost_kernel, (const void*)adaboost_warp_kernel})
+            TRY(raise_smem_limit(ab, device, g_fn[{ab, device}]));
         // the cluster boosting kernels: d + 1 features up to 11 blocks per cluster, above the
         // portable 8
         for (const void* fn : {(const void*)adaboost_cluster_kernel, (const void*)logitboost_cluster_kernel}) {
@@ -1085,14 +1088,23 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, lb_smem, st, &cluster));
         if (!cluster)
             return fail(BAP_EINVAL, "LogitBoost needs a cluster of %d blocks with %zu B of shared memory each", nF, lb_smem);
-    } else if (o->boost_form == 1) {
-        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, st, &cluster));
     }
-    o->last_boost_cluster = cluster ? 1 : 0;
+    // AdaBoost: the warp-per-feature block (form 2; by default only up to J = 2048, above which
+    // the cluster's per-block scans are shorter) when its shared memory fits, else the cluster
+    // (form 1) when the device can place it, else the one-block form
+    const size_t abw_smem = warp_boost_smem(J, nF);
+    bool warp_form = false;
     {
         std::lock_guard<std::mutex> lk(g_fn_mu);
         TRY(raise_smem_limit((const void*)adaboost_kernel, o->device, g_fn[{(const void*)adaboost_kernel, o->device}]));
+        FnInfo& fw = g_fn[{(const void*)adaboost_warp_kernel, o->device}];
+        TRY(raise_smem_limit((const void*)adaboost_warp_kernel, o->device, fw));
+        const bool want_warp = o->boost_form == 2 || (o->boost_form == 3 && J <= kWarpBoostAutoMaxJ);
+        warp_form = !logit && want_warp && abw_smem <= fw.max_dyn_smem;
     }
+    if (!logit && !warp_form && o->boost_form >= 1)
+        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, st, &cluster));
+    o->last_boost_form = logit ? 1 : warp_form ? 2 : cluster ? 1 : 0;
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
         const int ph_calc = phase_begin(o, PH_CALC);
@@ -1136,6 +1148,13 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
                                   o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
                                   o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
                                   o->rec_d.as<double>(), o->fitted.as<int>()));
+        } else if (warp_form) {
+            adaboost_warp_kernel<<<1, kWarpBoostThreads, abw_smem, st>>>(
+                o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label.as<int>(),
+                p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(), o->max_stumps,
+                o->n_stumps.as<int>(), o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+                o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(), o->rec_d.as<double>(),
+                o->fitted.as<int>());
         } else if (cluster) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -1317,14 +1336,14 @@ bap_status bap_set_wait_limit(bap_option* o, uint64_t ns) {
 
 bap_status bap_set_boost_form(bap_option* o, int form) {
     if (!o) return fail(BAP_EINVAL, "null option");
-    if (form != 0 && form != 1) return fail(BAP_EINVAL, "boost form outside 0..1");
+    if (form < 0 || form > 3) return fail(BAP_EINVAL, "boost form outside 0..3");
     o->boost_form = form;
     return BAP_OK;
 }
 
 bap_status bap_last_boost_form(const bap_option* o, int* form) {
     if (!o || !form) return fail(BAP_EINVAL, "null argument");
-    *form = o->last_boost_cluster;
+    *form = o->last_boost_form;
     return BAP_OK;
 }
 

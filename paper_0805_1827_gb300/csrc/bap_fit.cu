@@ -557,10 +557,6 @@ __global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int*
 // order.  The update multiplies each weight by exp(-alpha) or exp(+alpha), the two values
 // exp(-alpha y h) takes.
 
-__device__ inline bool key_less(double a, int ia, double b, int ib) {
-    return a < b || (a == b && ia < ib);
-}
-
 constexpr double kFix = 1152921504606846976.0;   // 2^60
 
 // round(v * 2^60) to the nearest integer, ties to even, for 0 <= v <= 1: the same value as
@@ -624,17 +620,6 @@ __device__ inline long long block_min_ll(long long v, long long* red) {
     return r;
 }
 
-__device__ inline double block_sum_d(double v, double* red) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    for (int k = 0; k < nw; ++k) r += red[k];
-    __syncthreads();
-    return r;
-}
-
 // Feature f of training point i: the d prices, then the payoff Phi in FP64 (the same
 // definition as the label epilogue of the path kernel).
 __device__ inline double cmc_feature(const DevModel* M, const double* X, int i, int f) {
@@ -658,25 +643,66 @@ __device__ inline double cmc_feature(const DevModel* M, const double* X, int i, 
     return v > 0 ? v : 0;
 }
 
-// Bitonic sort of (key, idx) pairs over P2 entries in shared memory, by (value, index).
+// Order-preserving map of a double's bits to an unsigned 64-bit integer (no NaN): the sign bit
+// set for values >= 0, every bit flipped for negative ones; -0 is taken as +0.  Integer compares
+// run on the integer pipe, where FP64 compares would queue for the narrow FP64 one.
+__device__ __forceinline__ unsigned long long ordered_from_bits(unsigned long long b) {
+    if ((b << 1) == 0) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ unsigned long long bits_from_ordered(unsigned long long k) {
+    return (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+}
+
+// One compare-exchange of the bitonic network: pair q of the stage (size, stride) joins entries
+// i and i + stride, i = q with a zero bit inserted at the stride, ascending where bit `size` of
+// i is clear.  Keys compare as (ordered value, index).
+__device__ __forceinline__ void bitonic_cmpx(unsigned long long* k, int* idx, int q, int stride,
+                                             int size) {
+    const int i = ((q & ~(stride - 1)) << 1) | (q & (stride - 1));
+    const int jx = i + stride;
+    const bool up = (i & size) == 0;
+    const unsigned long long a = k[i], b = k[jx];
+    const int ia = idx[i], ib = idx[jx];
+    const bool lt = b < a || (b == a && ib < ia);
+    if (lt == up) {
+        k[i] = b; k[jx] = a;
+        idx[i] = ib; idx[jx] = ia;
+    }
+}
+
+// Bitonic sort of (key, idx) pairs over P2 entries in shared memory, by (value, index), on the
+// ordered integer images of the values (the doubles are restored in place at the end).  A stage
+// whose pairs all lie inside one warp's chunk of P2 / warps entries runs under a warp barrier
+// only; a block barrier comes before the next stage that crosses chunks.
 __device__ inline void block_bitonic(double* key, int* idx, int P2) {
-    const int tid = threadIdx.x;
+    unsigned long long* k = reinterpret_cast<unsigned long long*>(key);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int i = tid; i < P2; i += blockDim.x) k[i] = ordered_from_bits(k[i]);
+    __syncthreads();
+    const int half = P2 >> 1;
+    const int chunk = P2 >= 2 * nwarps ? P2 / nwarps : 0;    // powers of two
+    bool pending = false;                                   // warp-local stages since a block barrier
     for (int size = 2; size <= P2; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < P2; i += blockDim.x) {
-                const int jx = i ^ stride;
-                if (jx > i) {
-                    const bool up = (i & size) == 0;
-                    const bool lt = key_less(key[jx], idx[jx], key[i], idx[i]);
-                    if (lt == up) {
-                        const double tk = key[i]; key[i] = key[jx]; key[jx] = tk;
-                        const int ti = idx[i]; idx[i] = idx[jx]; idx[jx] = ti;
-                    }
+            if (chunk > 0 && 2 * stride <= chunk) {
+                const int q0 = warp * (chunk >> 1), q1 = q0 + (chunk >> 1);
+                for (int q = q0 + lane; q < q1; q += 32) bitonic_cmpx(k, idx, q, stride, size);
+                __syncwarp();
+                pending = true;
+            } else {
+                if (pending) {
+                    __syncthreads();
+                    pending = false;
                 }
+                for (int q = tid; q < half; q += blockDim.x) bitonic_cmpx(k, idx, q, stride, size);
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
+    if (pending) __syncthreads();
+    for (int i = tid; i < P2; i += blockDim.x) k[i] = bits_from_ordered(k[i]);
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(1024) adaboost_kernel(
@@ -699,11 +725,10 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
     signed char* lab = reinterpret_cast<signed char*>(region + region_bytes);   // J
     long long* errl = reinterpret_cast<long long*>(err);                 // nF x J, -1 = no split
     __shared__ long long red_a[32], red_b[32], red_m[32];
-    __shared__ double red_d[32];
     __shared__ long long s_neg[MAXF];
     __shared__ double s_thr, s_fok, s_fbad;
     __shared__ int s_f, s_pol, s_stop, s_count;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // sort each feature (bitonic on (value, index)); the payoff feature is Phi in FP64 (the same
     // definition as the label epilogue of the path kernel)
@@ -792,65 +817,68 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
             c = block_min_ll(c, red_m);
             if (c != LLONG_MAX) { chosen = c; cf = f; }
         }
-        if (tid == 0) {
+        // the decision: lane 0 of warps 0, 1 and 2 (warp 0 the stopping rule and the record,
+        // warps 1 and 2 one update factor each)
+        if (lane == 0 && warp < 3) {
             const int f = cf < 0 ? 0 : cf;
             const long long c = cf < 0 ? 0 : chosen;
             long long e;
-            double th;
             int pl;
+            int i = 0;
             if (c < 2) {
-                th = -INFINITY;
                 pl = c == 0 ? 1 : -1;
                 e = c == 0 ? s_neg[f] : W - s_neg[f];
             } else {
-                const int i = (int)((c - 2) / 2);
+                i = (int)((c - 2) / 2);
                 pl = ((c - 2) % 2 == 0) ? 1 : -1;
                 const long long ep = errl[(size_t)f * J + i];
                 e = pl > 0 ? ep : W - ep;
-                th = 0.5 * (sorted_v[(size_t)f * J + i] + sorted_v[(size_t)f * J + i + 1]);
             }
-            const double eps = (double)e / (double)W;
-            s_stop = 0;
-            if (eps >= 0.5 - 1e-12) {
-                s_stop = 1;
+            if (cf < 0) e = W;                          // no candidate at all: stop below
+            if (warp == 0) {
+                const double eps = (double)e / (double)W;
+                s_stop = 0;
+                if (eps >= 0.5 - 1e-12) {
+                    s_stop = 1;
+                } else {
+                    const double th = c < 2 ? -INFINITY
+                                            : 0.5 * (sorted_v[(size_t)f * J + i] + sorted_v[(size_t)f * J + i + 1]);
+                    const int k = s_count++;
+                    feat[o_st + k] = f;
+                    thr[o_st + k] = th;
+                    pol[o_st + k] = pl;
+                    alpha[o_st + k] = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);   // log at the end
+                    s_f = f; s_thr = th; s_pol = pl;
+                    if (eps <= 1e-10) s_stop = 2;
+                }
+            } else if (warp == 1) {
+                s_fok = (0.5 * (double)W) / (double)(W - e);
             } else {
-                const double ec = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);
-                const double al = 0.5 * log((1.0 - ec) / ec);
-                const int k = s_count++;
-                feat[o_st + k] = f;
-                thr[o_st + k] = th;
-                pol[o_st + k] = pl;
-                alpha[o_st + k] = al;
-                s_f = f; s_thr = th; s_pol = pl;
-                s_fok = exp(-al);
-                s_fbad = exp(al);
-                if (eps <= 1e-10) s_stop = 2;
+                s_fbad = (0.5 * (double)W) / (double)e;
             }
         }
         __syncthreads();
-        if (s_stop == 1) break;
-        // w_i <- w_i exp(-alpha y_i h(x_i)), then normalise
+        if (s_stop != 0) break;
+        // the normalised update in closed form: 1 / (2 (1 - eps)) for a point the stump
+        // classifies right, 1 / (2 eps) for one it gets wrong
         {
             const int f = s_f;
             const double th = s_thr, fok = s_fok, fbad = s_fbad;
             const int pl = s_pol;
             const double* sv = sorted_v + (size_t)f * J;
             const int* six = sorted_i + (size_t)f * J;
-            double part2 = 0.0;
             for (int r = tid; r < J; r += blockDim.x) {
                 const int i = six[r];
                 const int h = sv[r] > th ? pl : -pl;
-                const double nw = w[i] * (h == lab[i] ? fok : fbad);
-                w[i] = nw;
-                part2 += nw;
+                w[i] *= (h == lab[i] ? fok : fbad);
             }
             __syncthreads();
-            const double Wn = block_sum_d(part2, red_d);
-            const double inv = 1.0 / Wn;
-            for (int i = tid; i < J; i += blockDim.x) w[i] *= inv;
-            __syncthreads();
         }
-        if (s_stop == 2) break;
+    }
+    __syncthreads();
+    for (int k = tid; k < s_count; k += blockDim.x) {
+        const double ec = alpha[o_st + k];
+        alpha[o_st + k] = 0.5 * log((1.0 - ec) / ec);
     }
     __syncthreads();
     if (tid == 0) {
@@ -909,9 +937,8 @@ __global__ void __launch_bounds__(512) adaboost_cluster_kernel(
     unsigned* cmask = mask + nwords;                                       // the chosen stump's
     __shared__ BoostExchange ex;                         // read remotely on the leader only
     __shared__ long long red_a[32], red_b[32];
-    __shared__ double red_d[32];
     __shared__ long long s_min, s_cand, s_lim, s_W;
-    __shared__ double s_thr, s_alpha, s_fok, s_fbad;
+    __shared__ double s_thr, s_ec, s_cok, s_cbad;
     __shared__ int s_f, s_pol, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     BoostExchange* lead = cluster.map_shared_rank(&ex, 0);
@@ -1042,37 +1069,33 @@ __global__ void __launch_bounds__(512) adaboost_cluster_kernel(
             }
         }
         cluster.sync();
-        // the chosen stump: the first feature with a candidate.  Thread 0 of every block reads
-        // the same leader values and takes the same decision; FP64 log/exp once per block.
-        if (tid == 0) {
+        // the chosen stump: the first feature with a candidate.  Lane 0 of warps 0, 1 and 2 of
+        // every block read the same leader values and take the same decision (warp 0 the
+        // stopping rule, warps 1 and 2 one update factor each, on three sub-partitions)
+        if (lane == 0 && warp < 3) {
             int cf = -1;
             long long cc = 0;
             for (int g = 0; g < nF && cf < 0; ++g) {
                 const long long v = lead->cand[g];
                 if (v != LLONG_MAX) { cf = g; cc = v; }
             }
-            const int fs0 = cf < 0 ? 0 : cf;
-            long long e;
-            double th0;
-            int pl0;
-            if (cf < 0) {
-                th0 = -INFINITY; pl0 = 1; e = Wl;     // no candidate at all: stop below
+            const long long e = cf < 0 ? Wl : lead->cerr[cf];     // no candidate at all: stop below
+            if (warp == 0) {
+                const double eps = (double)e / (double)Wl;
+                s_stop = 0;
+                if (eps >= 0.5 - 1e-12) {
+                    s_stop = 1;
+                } else {
+                    s_f = cf;
+                    s_thr = lead->cthr[cf];
+                    s_pol = (cc < 2) ? (cc == 0 ? 1 : -1) : (((cc - 2) % 2 == 0) ? 1 : -1);
+                    s_ec = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);
+                    if (eps <= 1e-10) s_stop = 2;
+                }
+            } else if (warp == 1) {
+                s_cok = (0.5 * (double)Wl) / (double)(Wl - e);
             } else {
-                e = lead->cerr[fs0];
-                th0 = lead->cthr[fs0];
-                pl0 = (cc < 2) ? (cc == 0 ? 1 : -1) : (((cc - 2) % 2 == 0) ? 1 : -1);
-            }
-            const double eps = (double)e / (double)Wl;
-            s_stop = 0;
-            if (eps >= 0.5 - 1e-12) {
-                s_stop = 1;
-            } else {
-                const double ec = fmin(fmax(eps, 1e-10), 1.0 - 1e-10);
-                const double al = 0.5 * log((1.0 - ec) / ec);
-                s_f = fs0; s_thr = th0; s_pol = pl0; s_alpha = al;
-                s_fok = exp(-al);
-                s_fbad = exp(al);
-                if (eps <= 1e-10) s_stop = 2;
+                s_cbad = (0.5 * (double)Wl) / (double)e;
             }
         }
         __syncthreads();
@@ -1083,43 +1106,333 @@ __global__ void __launch_bounds__(512) adaboost_cluster_kernel(
             feat[o_st + count] = fs;
             thr[o_st + count] = s_thr;
             pol[o_st + count] = pl;
-            alpha[o_st + count] = s_alpha;
+            alpha[o_st + count] = s_ec;                 // 1/2 ln((1 - eps) / eps) at the end
         }
         ++count;
+        if (s_stop == 2) break;
         {
             const unsigned* src = cluster.map_shared_rank(mask, fs);
             for (int wd = tid; wd < nwords; wd += blockDim.x) cmask[wd] = src[wd];
         }
         __syncthreads();
-        // w_i <- w_i exp(-alpha y_i h(x_i)), normalise, and the next round's fixed-point weights
-        // (the same order in every block)
+        // the normalised update in closed form (1 / (2 (1 - eps)) right, 1 / (2 eps) wrong) and
+        // the next round's fixed-point weights; no sum enters, so every block's copy is the same
         {
-            const double fok = s_fok, fbad = s_fbad;
-            double part2 = 0.0;
+            const double cok = s_cok, cbad = s_cbad;
             for (int i = tid; i < J; i += blockDim.x) {
                 const int h = ((cmask[i >> 5] >> (i & 31)) & 1u) ? pl : -pl;
-                const double nw = w[i] * (h == lab[i] ? fok : fbad);
-                w[i] = nw;
-                part2 += nw;
-            }
-            const double Wn = block_sum_d(part2, red_d);
-            const double invW = 1.0 / Wn;
-            for (int i = tid; i < J; i += blockDim.x) {
-                const double v = w[i] * invW;
+                const double v = w[i] * (h == lab[i] ? cok : cbad);
                 w[i] = v;
                 wf[i] = fix60(v);
             }
             __syncthreads();
         }
-        if (s_stop == 2) break;
     }
-    if (f == 0 && tid == 0) {
+    if (f == 0) {
+        for (int k = tid; k < count; k += blockDim.x) {
+            const double ec = alpha[o_st + k];
+            alpha[o_st + k] = 0.5 * log((1.0 - ec) / ec);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            n_stumps[m] = count;
+            stage_cmc_one(nF, count, feat + o_st, thr + o_st, pol + o_st, alpha + o_st, rec_len,
+                          rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
+            fitted[m] = 1;
+        }
+    }
+    cluster.sync();           // the leader's exchange area and the masks stay until all are done
+}
+
+// ---------------------------------------------------------------------------------------------
+// [class] The same AdaBoost fit in one 512-thread block, one warp per feature.  A feature's
+// sorted order sits in shared memory as 16-bit point indices (the top bit marks a position after
+// which a threshold can sit) and the weights as signed fixed-point values s_i = lab_i wf_i in
+// point order.  The error of polarity +1 at split r of feature f is neg_f + S_f(r), S_f the
+// prefix of s along f's order, so a round costs the warp of f one gather per position.  Lane l
+// owns positions 32 l .. 32 l + 31 of every 1024, stored transposed so that the warp's loads are
+// conflict free; per segment of 32 the warp keeps the prefix at its start and the least and
+// largest prefix at a split.  Those give the feature's least error, min(neg + min S,
+// W - neg - max S), and, once the round's least error is known, the first segment holding a
+// candidate, which the whole warp rescans.  Choices, tie rule and weight update are those of
+// adaboost_cluster_kernel, the update in the same thread layout and summation order, so the
+// stumps are the cluster form's bit for bit; the FP64 division, log and exp of a round run on
+// one thread.
+
+// Storage index of sorted position r (and, the map being its own inverse, the position held at
+// storage index r): the two 5-bit fields below bit 10 swapped.
+__device__ __forceinline__ int warp_boost_tpos(int r) {
+    return (r & ~1023) | ((r & 31) << 5) | ((r >> 5) & 31);
+}
+
+__global__ void __launch_bounds__(kWarpBoostThreads) adaboost_warp_kernel(
+    const DevModel* M, int m, int J, const double* X, const int* label, int n_rounds,
+    double* sorted_v, int* sorted_i, int max_stumps, int* n_stumps, int* feat, double* thr,
+    int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d, int* fitted) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const unsigned FULL = 0xffffffffu;
+    constexpr int nthr = kWarpBoostThreads;
+    const int d = M->d;
+    const int nF = d + 1;
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    const int nsc = (J + 1023) >> 10;              // blocks of 1024 sorted positions
+    const int NP = nsc << 10;                      // stored positions per feature
+    const int nseg = nF * nsc * 32;
+    // shared memory: region (sort keys, then w | s) | pos | segment base, min, max | lab
+    const size_t ra = warp_boost_region(J);
+    double* key = reinterpret_cast<double*>(smem);                        // P2 (sorting only)
+    int* idx = reinterpret_cast<int*>(key + P2);                          // P2 (sorting only)
+    double* w = reinterpret_cast<double*>(smem);                          // J FP64 weights
+    long long* sw = reinterpret_cast<long long*>(smem + (size_t)J * 8);  // J + 1 (s_J = 0: padding)
+    unsigned short* pos = reinterpret_cast<unsigned short*>(smem + ra);   // nF x NP
+    long long* sg_base = reinterpret_cast<long long*>(smem + ra + (size_t)nF * NP * 2);
+    long long* sg_min = sg_base + nseg;
+    long long* sg_max = sg_min + nseg;
+    signed char* lab = reinterpret_cast<signed char*>(sg_max + nseg);    // J
+    __shared__ long long s_fmin[MAXF], s_fneg[MAXF], s_cand[MAXF], s_cerr[MAXF];
+    __shared__ double s_cthr[MAXF];
+    __shared__ unsigned long long s_W;
+    __shared__ double s_cok, s_cbad, s_Wd, s_hWd;
+    __shared__ int s_f, s_pol, s_stop, s_rstar;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // sort every feature (bitonic on (value, index), the whole block per feature); publish it
+    // and keep its order, with the split marks, in shared memory
+    for (int f = 0; f < nF; ++f) {
+        for (int i = tid; i < P2; i += nthr) {
+            key[i] = i < J ? cmc_feature(M, X, i, f) : INFINITY;
+            idx[i] = i < J ? i : 0x7fffffff;
+        }
+        __syncthreads();
+        block_bitonic(key, idx, P2);
+        for (int r = tid; r < NP; r += nthr) {
+            unsigned short u = (unsigned short)J;          // padding: the zero-weight point J
+            if (r < J) {
+                sorted_v[(size_t)f * J + r] = key[r];
+                sorted_i[(size_t)f * J + r] = idx[r];
+                // (a padding index can only sort below J if a feature were NaN: it then maps to
+                // the zero-weight point J, so no access leaves the arrays)
+                const int k = idx[r] < J ? idx[r] : J;
+                u = (unsigned short)(k | ((r < J - 1 && key[r + 1] > key[r]) ? 0x8000 : 0));
+            }
+            pos[(size_t)f * NP + warp_boost_tpos(r)] = u;
+        }
+        __syncthreads();
+    }
+    const long long w0 = fix60(1.0 / (double)J);
+    for (int i = tid; i < J; i += nthr) {
+        w[i] = 1.0 / (double)J;
+        const signed char l = label[i] > 0 ? 1 : -1;
+        lab[i] = l;
+        sw[i] = l > 0 ? w0 : -w0;
+    }
+    if (tid == 0) {
+        sw[J] = 0;
+        s_W = (unsigned long long)(w0 * (long long)J);
+        s_stop = 0;
+    }
+    __syncthreads();
+
+    const long long tol = (long long)(1e-12 * kFix);
+    const size_t o_st = (size_t)m * max_stumps;
+    int count = 0;
+    for (int round = 0; round < n_rounds; ++round) {
+        const long long W = (long long)s_W;            // exact total of the fixed-point weights
+        // the round's W in FP64 for the decision, off its path (the last warp owns no feature)
+        if (tid == nthr - 32) {
+            s_Wd = (double)W;
+            s_hWd = 0.5 * (double)W;
+        }
+        // pass 1 (warp f): prefix sums along feature f's order; the negatives' total follows
+        // from W and the signed total
+        if (warp < nF) {
+            const int f = warp;
+            const unsigned short* P = pos + (size_t)f * NP;
+            long long carry = 0, amin = LLONG_MAX, amax = LLONG_MIN;
+            for (int sc = 0; sc < nsc; ++sc) {
+                const unsigned short* Q = P + (sc << 10) + lane;
+                long long T = 0, tmin = LLONG_MAX, tmax = LLONG_MIN;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const unsigned u = Q[j << 5];
+                    T += sw[u & 0x7fffu];
+                    if (u & 0x8000u) {
+                        tmin = min(tmin, T);
+                        tmax = max(tmax, T);
+                    }
+                }
+                long long incl = T;
+                for (int off = 1; off < 32; off <<= 1) {
+                    const long long t = __shfl_up_sync(FULL, incl, off);
+                    if (lane >= off) incl += t;
+                }
+                const long long base = carry + incl - T;
+                carry += __shfl_sync(FULL, incl, 31);
+                const long long smn = tmin == LLONG_MAX ? LLONG_MAX : base + tmin;
+                const long long smx = tmax == LLONG_MIN ? LLONG_MIN : base + tmax;
+                const int s = (f * nsc + sc) * 32 + lane;
+                sg_base[s] = base;
+                sg_min[s] = smn;
+                sg_max[s] = smx;
+                amin = min(amin, smn);
+                amax = max(amax, smx);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                amin = min(amin, __shfl_xor_sync(FULL, amin, off));
+                amax = max(amax, __shfl_xor_sync(FULL, amax, off));
+            }
+            const long long neg = (W - carry) / 2;      // W - S = 2 (negatives' weight), exact
+            long long mn = min(neg, W - neg);
+            if (amin != LLONG_MAX) mn = min(mn, neg + amin);
+            if (amax != LLONG_MIN) mn = min(mn, W - (neg + amax));
+            if (lane == 0) {
+                s_fmin[f] = mn;
+                s_fneg[f] = neg;
+            }
+        }
+        __syncthreads();
+        // pass 2 (warp f): the first candidate of feature f within the tolerance of the least
+        // error over all features
+        if (warp < nF) {
+            const int f = warp;
+            long long emin = LLONG_MAX;
+            for (int g = 0; g < nF; ++g) emin = min(emin, s_fmin[g]);
+            const long long lim = emin + tol;
+            const long long neg = s_fneg[f];
+            long long c = LLONG_MAX, e = 0;
+            int r0 = -1;
+            if (neg <= lim) {
+                c = 0;
+                e = neg;
+            } else if (W - neg <= lim) {
+                c = 1;
+                e = W - neg;
+            } else {
+                for (int sc = 0; sc < nsc && c == LLONG_MAX; ++sc) {
+                    const int s0 = (f * nsc + sc) * 32;
+                    const long long smn = sg_min[s0 + lane], smx = sg_max[s0 + lane];
+                    const bool hit = (smn != LLONG_MAX && neg + smn <= lim) ||
+                                     (smx != LLONG_MIN && W - (neg + smx) <= lim);
+                    const unsigned b = __ballot_sync(FULL, hit);
+                    if (!b) continue;
+                    // the first such segment, rescanned by the warp: lane j takes its position j
+                    const int L = __ffs(b) - 1;
+                    const unsigned u = pos[(size_t)f * NP + (sc << 10) + (lane << 5) + L];
+                    long long incl = sw[u & 0x7fffu];
+                    for (int off = 1; off < 32; off <<= 1) {
+                        const long long t = __shfl_up_sync(FULL, incl, off);
+                        if (lane >= off) incl += t;
+                    }
+                    const long long er = neg + sg_base[s0 + L] + incl;
+                    const bool q = (u & 0x8000u) && (er <= lim || W - er <= lim);
+                    const unsigned bq = __ballot_sync(FULL, q);
+                    if (!bq) continue;                     // not reached: the segment holds one
+                    const int j = __ffs(bq) - 1;
+                    const long long ej = __shfl_sync(FULL, er, j);
+                    r0 = (sc << 10) + (L << 5) + j;
+                    if (ej <= lim) {
+                        c = 2 + 2LL * r0;
+                        e = ej;
+                    } else {
+                        c = 3 + 2LL * r0;
+                        e = W - ej;
+                    }
+                }
+            }
+            if (lane == 0) {
+                s_cand[f] = c;
+                s_cerr[f] = e;
+                s_cthr[f] = r0 >= 0 ? (double)r0 : -INFINITY;    // the position; value at the end
+            }
+        }
+        __syncthreads();
+        // the chosen stump: the first feature with a candidate.  Lane 0 of warps 0, 1 and 2
+        // (three sub-partitions) take the same decision and one FP64 quotient each: eps = e / W
+        // with the stopping rule and the record, and the update factors 1 / (2 (1 - eps)) =
+        // (W / 2) / (W - e) and 1 / (2 eps) = (W / 2) / e
+        if (lane == 0 && warp < 3) {
+            int cf = -1;
+            long long cc = 0;
+            for (int g = 0; g < nF && cf < 0; ++g) {
+                if (s_cand[g] != LLONG_MAX) {
+                    cf = g;
+                    cc = s_cand[g];
+                }
+            }
+            const long long ce = cf < 0 ? W : s_cerr[cf];     // no candidate at all: stop below
+            if (warp == 0) {
+                const double eps = (double)ce / s_Wd;
+                s_stop = 0;
+                if (eps >= 0.5 - 1e-12) {
+                    s_stop = 1;
+                } else {
+                    const int pl0 = (cc < 2) ? (cc == 0 ? 1 : -1) : (((cc - 2) % 2 == 0) ? 1 : -1);
+                    s_f = cf;
+                    s_pol = pl0;
+                    s_rstar = cc >= 2 ? (int)((cc - 2) / 2) : -1;
+                    feat[o_st + count] = cf;
+                    thr[o_st + count] = s_cthr[cf];
+                    pol[o_st + count] = pl0;
+                    alpha[o_st + count] = eps;                 // clamped, and its log, at the end
+                    if (eps <= 1e-10) s_stop = 2;
+                }
+                s_W = 0ull;                                // every thread holds this round's W
+            } else if (warp == 1) {
+                s_cok = s_hWd / (double)(W - ce);
+            } else {
+                s_cbad = s_hWd / (double)ce;
+            }
+        }
+        __syncthreads();
+        if (s_stop != 0) break;
+        ++count;
+        // the normalised AdaBoost update in closed form: exp(-+alpha) / Z is 1 / (2 (1 - eps))
+        // for a point the stump classifies right and 1 / (2 eps) for one it gets wrong.  No sum
+        // enters, so the order is free: walk the chosen feature's stored order, whose position
+        // tells the stump's vote
+        {
+            const int rstar = s_rstar, pl = s_pol;
+            const double cok = s_cok, cbad = s_cbad;
+            const unsigned short* P = pos + (size_t)s_f * NP;
+            long long ws = 0;
+            for (int k = tid; k < NP; k += nthr) {
+                const int r = warp_boost_tpos(k);
+                const int i = P[k] & 0x7fff;
+                if (r < J && i < J) {
+                    const int h = r > rstar ? pl : -pl;
+                    const double v = w[i] * (h == lab[i] ? cok : cbad);
+                    w[i] = v;
+                    const long long q = fix60(v);
+                    sw[i] = lab[i] > 0 ? q : -q;
+                    ws += q;
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) ws += __shfl_down_sync(FULL, ws, off);
+            if (lane == 0) atomicAdd(&s_W, (unsigned long long)ws);
+        }
+        __syncthreads();
+    }
+    // a stump that stopped the fit with eps <= 1e-10 is kept (count it); then, one thread per
+    // stump, alpha = 1/2 ln((1 - eps) / eps) and the threshold between sorted positions r, r + 1
+    if (s_stop == 2) ++count;
+    for (int k = tid; k < count; k += nthr) {
+        const double ec = fmin(fmax(alpha[o_st + k], 1e-10), 1.0 - 1e-10);
+        alpha[o_st + k] = 0.5 * log((1.0 - ec) / ec);
+        const double t = thr[o_st + k];
+        if (t >= 0.0) {
+            const double* sv = sorted_v + (size_t)feat[o_st + k] * J;
+            const int r = (int)t;
+            thr[o_st + k] = 0.5 * (sv[r] + sv[r + 1]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
         n_stumps[m] = count;
         stage_cmc_one(nF, count, feat + o_st, thr + o_st, pol + o_st, alpha + o_st, rec_len,
                       rec_f + (size_t)m * rec_len, rec_d + (size_t)m * rec_len);
         fitted[m] = 1;
     }
-    cluster.sync();           // the leader's exchange area and the masks stay until all are done
 }
 
 // ---------------------------------------------------------------------------------------------

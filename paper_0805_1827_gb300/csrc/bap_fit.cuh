@@ -33,6 +33,30 @@ __global__ void adaboost_cluster_kernel(const DevModel* M, int m, int J, const d
                                         int* sorted_i, int max_stumps, int* n_stumps, int* feat,
                                         double* thr, int* pol, double* alpha, int rec_len,
                                         float* rec_f, double* rec_d, int* fitted);
+// One-block AdaBoost with one warp per feature: threads per block, and the dynamic shared memory
+// for J points and nF features (the sort region, later the FP64 and signed fixed-point weights;
+// the 16-bit sorted orders in blocks of 1024 positions; three 64-bit values per segment of 32;
+// the labels).
+constexpr int kWarpBoostThreads = 512;
+// Largest J for which the default boosting form picks the warp-per-feature block over the
+// cluster (measured on GB300: the block is faster at J = 1024, the cluster at J = 4000).
+constexpr int kWarpBoostAutoMaxJ = 2048;
+__host__ __device__ inline size_t warp_boost_region(int J) {
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    const size_t a = (size_t)P2 * 12, b = (size_t)J * 16 + 8;
+    return ((a > b ? a : b) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t warp_boost_smem(int J, int nF) {
+    const size_t nsc = (size_t)(J + 1023) / 1024;
+    return warp_boost_region(J) + (size_t)nF * nsc * 1024 * 2 + 3 * (size_t)nF * nsc * 32 * 8 +
+           (size_t)J;
+}
+__global__ void adaboost_warp_kernel(const DevModel* M, int m, int J, const double* X,
+                                     const int* label, int n_rounds, double* sorted_v,
+                                     int* sorted_i, int max_stumps, int* n_stumps, int* feat,
+                                     double* thr, int* pol, double* alpha, int rec_len,
+                                     float* rec_f, double* rec_d, int* fitted);
 __global__ void logitboost_cluster_kernel(const DevModel* M, int m, int J, const double* X,
                                           const int* label, int n_rounds, double* sorted_v,
                                           int* sorted_i, int max_stumps, int* n_stumps, int* feat,

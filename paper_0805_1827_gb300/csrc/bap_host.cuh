@@ -145,8 +145,8 @@ struct bap_option {
     int launch_mode = bap::LAUNCH_GRAPH;
     int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device
     unsigned long long wait_limit_ns = 0;   // grid-barrier wait bound; 0: automatic
-    int boost_form = 1;           // CMC boosting: 1 cluster of d+1 blocks, 0 one block
-    int last_boost_cluster = 0;   // form the last CMC fit ran
+    int boost_form = 3;           // CMC boosting: 3 by J, 2 warp per feature, 1 cluster, 0 one block
+    int last_boost_form = 0;      // form the last CMC fit ran
     cudaGraphExec_t graph_exec = nullptr;
     bap_iz_params graph_params{};
     int graph_failed = 0;
