@@ -325,15 +325,34 @@ def launch_forms(bap, params, stream) -> dict:
 
 
 def cmc_boost_forms(bap, stream) -> dict:
-    """The CMC fit of the 7-asset basket put (J=4000 training points, N2=2e4 inner paths, 200
-    stumps, 9 fitted dates) with the boosting in one warp-per-feature block, on a cluster of d+1
-    blocks and in one 1024-thread block; device time of the fit from the library's events, and
-    the same price from all three."""
-    from bap_workloads import CMCParams, spec_basket_put_7
+    """The CMC boosting forms side by side (one warp-per-feature block, a cluster of d+1 blocks,
+    one 1024-thread block): first the serving-sized fit (5-asset max-call, J=1024 points, N2=200,
+    200 stumps, 10 fitted dates; boosting time per date from the library's phase events), then
+    the 7-asset basket put (J=4000, N2=2e4, 200 stumps, 9 fitted dates; device time of the whole
+    fit).  Every form gives the same price."""
+    from bap_workloads import CMCParams, spec_basket_put_7, spec_max_call
+    names = {0: "one_block", 1: "cluster", 2: "warp_per_feature"}
+    small = {}
+    sspec = spec_max_call(5, 100.0, rho=0.3, n_dates=11, T=2.0)
+    sparams = CMCParams(J=1024, N2=200, n_stumps=200, seed=1)
+    for name, form in (("warp_per_feature", 2), ("cluster", 1), ("one_block", 0)):
+        best = None
+        for rep in range(2):
+            o = bap.Option(sspec, stream=stream.cuda_stream)
+            o.set_profiling(True)
+            o.set_boost_form(form)
+            o.fit_classifier(sparams)
+            r = o.price(100_000, 5)
+            o.close()
+            if best is None or r["phase_ms"][2] < best["phase_ms"][2]:
+                best = r
+        small[name] = {"boost_ms_per_date": best["phase_ms"][2] / (sspec.n_dates - 1),
+                       "fit_ms": best["fit_ms"], "price": best["price"]}
+    small["identical_prices"] = len({small[k]["price"] for k in names.values()}) == 1
+    small["workload"] = "5-asset max-call, CMC, J=1024, N2=200, 200 stumps, 10 fitted dates"
     spec = spec_basket_put_7(0)
     params = CMCParams(J=4000, N2=20_000, n_stumps=200, seed=1)
-    out = {}
-    names = {0: "one_block", 1: "cluster", 2: "warp_per_feature"}
+    out = {"J1024": small}
     for name, form in (("warp_per_feature", 2), ("cluster", 1), ("one_block", 0)):
         best = None
         for rep in range(2):
