@@ -1489,6 +1489,7 @@ __global__ void __launch_bounds__(512) logitboost_cluster_kernel(
     __shared__ LogitExchange ex;
     __shared__ long long red_a[32], red_b[32];
     __shared__ unsigned long long s_gmax;
+    __shared__ unsigned s_gmax32;
     __shared__ int s_first, s_f, s_const, s_stop;
     __shared__ double s_lim, s_thr, s_cl, s_cr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -1530,7 +1531,7 @@ __global__ void __launch_bounds__(512) logitboost_cluster_kernel(
             wq[i] = __double2ll_rn(w * kLbFix);
             sq[i] = __double2ll_rn((w * z) * kLbFix);
         }
-        if (tid == 0) { s_gmax = 0ULL; s_first = 0x7fffffff; }
+        if (tid == 0) { s_gmax = 0ULL; s_gmax32 = 0u; s_first = 0x7fffffff; }
         cluster.sync();
         // the other blocks' slices
         for (int g = 0; g < nF; ++g) {
@@ -1557,6 +1558,28 @@ __global__ void __launch_bounds__(512) logitboost_cluster_kernel(
             const long long WR = W - WL, SR = S - SL;
             return (double)SL * (double)SL / (double)WL + (double)SR * (double)SR / (double)WR;
         };
+        // The same gain in FP32 (relative error below 4e-7: four conversions, two squares, two
+        // divisions and an add, each correctly rounded), used as a filter: a split whose FP32
+        // gain is below (1 - 8e-6) times the block's largest FP32 gain is at least 1e-12 below
+        // the block's largest exact gain, hence below the tolerance of the overall largest, so
+        // the exact FP64 gain is taken only for the splits that pass (the choice is unchanged).
+        auto gain32 = [&](long long WL, long long SL) -> float {
+            const float a = (float)WL, b = (float)SL, ra = (float)(W - WL), sb = (float)(S - SL);
+            return b * b / a + sb * sb / ra;
+        };
+        {
+            float my32 = 0.0f;
+            long long a = pw0, b = ps0;
+            for (int r = lo; r < hi; ++r) {
+                const int k = six[r];
+                a += wq[k];
+                b += sq[k];
+                if (split[r] && a > 0 && W - a > 0) my32 = fmaxf(my32, gain32(a, b));
+            }
+            atomicMax(&s_gmax32, __float_as_uint(my32));   // gains are >= 0: bits order as values
+        }
+        __syncthreads();
+        const float flt = __uint_as_float(s_gmax32) * (1.0f - 8e-6f);
         unsigned long long my = 0ULL;
         {
             long long a = pw0, b = ps0;
@@ -1564,7 +1587,7 @@ __global__ void __launch_bounds__(512) logitboost_cluster_kernel(
                 const int k = six[r];
                 a += wq[k];
                 b += sq[k];
-                if (split[r] && a > 0 && W - a > 0) {
+                if (split[r] && a > 0 && W - a > 0 && gain32(a, b) >= flt) {
                     const unsigned long long gb = (unsigned long long)__double_as_longlong(gain(a, b));
                     my = gb > my ? gb : my;
                 }
@@ -1598,7 +1621,7 @@ __global__ void __launch_bounds__(512) logitboost_cluster_kernel(
                 const int k = six[r];
                 a += wq[k];
                 b += sq[k];
-                if (split[r] && a > 0 && W - a > 0 && gain(a, b) >= lim) {
+                if (split[r] && a > 0 && W - a > 0 && gain32(a, b) >= flt && gain(a, b) >= lim) {
                     rfirst = r;
                     a_at = a;
                     b_at = b;
