@@ -1000,11 +1000,15 @@ bap_status finish_fit_iz(bap_option* o) {
     return o->last_noconv > 0 ? BAP_ENOCONV : BAP_OK;
 }
 
-// Launch configuration of the cluster AdaBoost: one cluster of nF blocks of 512 threads.
+// Threads per block of the cluster boosting kernels for J points: 1024 above J = 2048 (shorter
+// per-thread scans), else 512 (measured faster at J = 1024).  The stumps do not depend on it.
+int cluster_boost_threads(int J) { return J > 2048 ? kClusterBoostThreads : kClusterBoostThreads / 2; }
+
+// Launch configuration of the cluster boosting kernels: one cluster of nF blocks.
 void boost_cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int nF, size_t smem,
-                          cudaStream_t st) {
+                          cudaStream_t st, int threads) {
     cfg.gridDim = dim3((unsigned)nF);
-    cfg.blockDim = dim3(512);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1017,17 +1021,17 @@ void boost_cluster_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, in
 
 // Whether a cluster of nF blocks of this boosting kernel fits on the device (cached per kernel,
 // device, nF and size).
-bap_status boost_cluster_fits(const void* fn, int device, int nF, size_t smem, cudaStream_t st,
-                              bool* ok) {
+bap_status boost_cluster_fits(const void* fn, int device, int nF, size_t smem, int threads,
+                              cudaStream_t st, bool* ok) {
     static std::mutex mu;
-    static std::map<std::tuple<const void*, int, int, size_t>, bool> known;
+    static std::map<std::tuple<const void*, int, int, size_t, int>, bool> known;
     std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_tuple(fn, device, nF, smem);
+    const auto key = std::make_tuple(fn, device, nF, smem, threads);
     auto it = known.find(key);
     if (it == known.end()) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
-        boost_cluster_config(cfg, attr, nF, smem, st);
+        boost_cluster_config(cfg, attr, nF, smem, st, threads);
         int n = 0;
         const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
         if (e != cudaSuccess) cudaGetLastError();
@@ -1080,12 +1084,13 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     const size_t abc_smem = (size_t)J * 10 + std::max((size_t)P2 * 12, (size_t)J * 16) + 4 +
                             8 * (size_t)((J + 31) / 32);
     bool cluster = false;
+    const int cl_threads = cluster_boost_threads(J);
     // LogitBoost: one cluster of nF blocks (the slices of F, the sums, both permutations)
     const size_t ns_lb = (size_t)((J + nF - 1) / nF);
     const size_t lb_smem = ns_lb * 8 + std::max((size_t)P2 * 12, (size_t)J * 24) + 2 * (size_t)J + 4 +
                            4 * (size_t)((J + 31) / 32);
     if (logit) {
-        TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, lb_smem, st, &cluster));
+        TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, lb_smem, cl_threads, st, &cluster));
         if (!cluster)
             return fail(BAP_EINVAL, "LogitBoost needs a cluster of %d blocks with %zu B of shared memory each", nF, lb_smem);
     }
@@ -1103,7 +1108,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         warp_form = !logit && want_warp && abw_smem <= fw.max_dyn_smem;
     }
     if (!logit && !warp_form && o->boost_form >= 1)
-        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, st, &cluster));
+        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, cl_threads, st, &cluster));
     o->last_boost_form = logit ? 1 : warp_form ? 2 : cluster ? 1 : 0;
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
@@ -1140,7 +1145,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         if (logit) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
-            boost_cluster_config(cfg, attr, nF, lb_smem, st);
+            boost_cluster_config(cfg, attr, nF, lb_smem, st, cl_threads);
             CU(cudaLaunchKernelEx(&cfg, logitboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
                                   m, J, (const double*)o->start.as<double>(),
                                   (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
@@ -1158,7 +1163,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         } else if (cluster) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
-            boost_cluster_config(cfg, attr, nF, abc_smem, st);
+            boost_cluster_config(cfg, attr, nF, abc_smem, st, cl_threads);
             CU(cudaLaunchKernelEx(&cfg, adaboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
                                   m, J, (const double*)o->start.as<double>(),
                                   (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),

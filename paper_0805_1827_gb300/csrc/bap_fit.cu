@@ -908,7 +908,7 @@ struct BoostExchange {
     double cthr[MAXF];             // its threshold
 };
 
-__global__ void __launch_bounds__(512) adaboost_cluster_kernel(
+__global__ void __launch_bounds__(kClusterBoostThreads) adaboost_cluster_kernel(
     const DevModel* M, int m, int J, const double* X, const int* label, int n_rounds,
     double* sorted_v, int* sorted_i, int max_stumps, int* n_stumps, int* feat, double* thr,
     int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d, int* fitted) {
@@ -1457,7 +1457,7 @@ struct LogitExchange {
     double cthr[MAXF], ccl[MAXF], ccr[MAXF];
 };
 
-__global__ void __launch_bounds__(512) logitboost_cluster_kernel(
+__global__ void __launch_bounds__(kClusterBoostThreads) logitboost_cluster_kernel(
     const DevModel* M, int m, int J, const double* X, const int* label, int n_rounds,
     double* sorted_v, int* sorted_i, int max_stumps, int* n_stumps, int* feat, double* thr,
     int* pol, double* alpha, int rec_len, float* rec_f, double* rec_d, int* fitted) {

@@ -28,6 +28,8 @@ __global__ void adaboost_kernel(const DevModel* M, int m, int J, const double* X
                                 double* sorted_v, int* sorted_i, double* err, int max_stumps,
                                 int* n_stumps, int* feat, double* thr, int* pol, double* alpha,
                                 int rec_len, float* rec_f, double* rec_d, int* fitted);
+// Threads per block of the cluster boosting kernels (one block per feature).
+constexpr int kClusterBoostThreads = 1024;
 __global__ void adaboost_cluster_kernel(const DevModel* M, int m, int J, const double* X,
                                         const int* label, int n_rounds, double* sorted_v,
                                         int* sorted_i, int max_stumps, int* n_stumps, int* feat,
