@@ -378,48 +378,78 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
             else rhs[r] = acc[k];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double dsc[MAXCOEF];
-            bool ok = true;
-            for (int i = 0; i < P; ++i) {
-                dsc[i] = G[i * P + i] > 0 ? 1.0 / sqrt(G[i * P + i]) : 0.0;
-                if (dsc[i] == 0.0) ok = false;
-            }
-            if (ok) {
-                for (int i = 0; i < P; ++i)
-                    for (int k = 0; k < P; ++k) G[i * P + k] *= dsc[i] * dsc[k];
-                // Cholesky G = R R^T (lower, in place)
-                for (int jj = 0; jj < P && ok; ++jj) {
-                    double v = G[jj * P + jj];
-                    for (int k = 0; k < jj; ++k) v -= G[jj * P + k] * G[jj * P + k];
-                    if (!(v > 1e-13)) { ok = false; break; }
-                    const double l = sqrt(v);
-                    G[jj * P + jj] = l;
-                    for (int i = jj + 1; i < P; ++i) {
-                        double w = G[i * P + jj];
-                        for (int k = 0; k < jj; ++k) w -= G[i * P + k] * G[jj * P + k];
-                        G[i * P + jj] = w / l;
+        // Scale to a unit diagonal, factor G = L L^T (lower, in place) with the rank test on the
+        // pivots, and solve.  The block shares the work; every entry receives the same
+        // operations in the same order as in a one-thread left-looking factorisation (entry
+        // (i, j) starts from its scaled value and subtracts L[i][k] L[j][k] for k = 0, 1, ...,
+        // j - 1), so the coefficients are those of that sequential form bit for bit.
+        __shared__ double dsc[MAXCOEF];
+        __shared__ double s_l;
+        __shared__ int s_ok;
+        const int tid = threadIdx.x, nth = blockDim.x;
+        if (tid == 0) s_ok = 1;
+        __syncthreads();
+        for (int i = tid; i < P; i += nth) {
+            dsc[i] = G[i * P + i] > 0 ? 1.0 / sqrt(G[i * P + i]) : 0.0;
+            if (dsc[i] == 0.0) s_ok = 0;
+        }
+        __syncthreads();
+        bool ok = s_ok != 0;
+        if (ok) {
+            for (int e = tid; e < P * P; e += nth) G[e] *= dsc[e / P] * dsc[e % P];
+            __syncthreads();
+            // right-looking: column jj's pivot, the column below it, then the trailing triangle
+            for (int jj = 0; jj < P; ++jj) {
+                if (tid == 0) {
+                    const double v = G[jj * P + jj];
+                    if (!(v > 1e-13)) {
+                        s_ok = 0;
+                    } else {
+                        s_l = sqrt(v);
+                        G[jj * P + jj] = s_l;
                     }
                 }
-            }
-            if (ok) {
-                double z[MAXCOEF];
-                for (int i = 0; i < P; ++i) {
-                    double v = rhs[i] * dsc[i];
-                    for (int k = 0; k < i; ++k) v -= G[i * P + k] * z[k];
-                    z[i] = v / G[i * P + i];
+                __syncthreads();
+                if (!s_ok) break;
+                const double l = s_l;
+                for (int i = jj + 1 + tid; i < P; i += nth) G[i * P + jj] = G[i * P + jj] / l;
+                __syncthreads();
+                const int n = P - 1 - jj;                 // trailing rows and columns jj+1..P-1
+                for (int e = tid; e < n * (n + 1) / 2; e += nth) {
+                    int i = 0, rem = e;                   // row i (0-based in the trailing part)
+                    while (rem > i) { rem -= i + 1; ++i; }
+                    const int r = jj + 1 + i, c = jj + 1 + rem;      // c <= r
+                    G[r * P + c] -= G[r * P + jj] * G[c * P + jj];
                 }
+                __syncthreads();
+            }
+            ok = s_ok != 0;
+        }
+        if (ok) {
+            // forward: z = L^-1 (dsc * rhs), column by column (row i subtracts in k order)
+            for (int i = tid; i < P; i += nth) rhs[i] *= dsc[i];
+            __syncthreads();
+            for (int k = 0; k < P; ++k) {
+                if (tid == 0) rhs[k] = rhs[k] / G[k * P + k];
+                __syncthreads();
+                const double zk = rhs[k];
+                for (int i = k + 1 + tid; i < P; i += nth) rhs[i] -= G[i * P + k] * zk;
+                __syncthreads();
+            }
+            // backward: L^T coef = z, one thread (each row sums in ascending k)
+            if (tid == 0) {
                 for (int i = P - 1; i >= 0; --i) {
-                    double v = z[i];
+                    double v = rhs[i];
                     for (int k = i + 1; k < P; ++k) v -= G[k * P + i] * coef[k];
                     coef[i] = v / G[i * P + i];
                 }
                 for (int i = 0; i < P; ++i) coef[i] *= dsc[i];
-            } else {
-                for (int i = 0; i < P; ++i) coef[i] = 0.0;
-                coef[0] = mean;
             }
+        } else if (tid == 0) {
+            for (int i = 0; i < P; ++i) coef[i] = 0.0;
+            coef[0] = mean;
         }
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (n_used == 0) {
