@@ -202,10 +202,20 @@ def cpu_baseline() -> dict:
     res = oracle.price(spec, rules, CPU_NPRICE, 1, n_threads=cores)
     el = time.perf_counter() - t
     steps = sum(d["steps"] for d in diag.values()) + res["path_steps"]
+    # the same oracle on one thread, on a quarter of the items and a fifth of the pricing paths
+    p1 = IZParams(J=CPU_J // 4, N1=CPU_N1, degree=2, seed=0)
+    t = time.perf_counter()
+    rules1, diag1 = oracle.iz_fit(spec, p1, n_threads=1)
+    res1 = oracle.price(spec, rules1, CPU_NPRICE // 5, 1, n_threads=1)
+    el1 = time.perf_counter() - t
+    steps1 = sum(d["steps"] for d in diag1.values()) + res1["path_steps"]
     return {"value": steps / el, "unit": "path-steps/s", "cores": cores, "kind": "oracle",
             "sample": (f"I&Z fit of the 5-asset max-call (rho=0.3, S0=100, 9 dates) at "
                        f"J={CPU_J}, N1={CPU_N1}, 8 fitted dates + {CPU_NPRICE} pricing paths "
-                       f"({steps} path-steps in {el:.1f} s); FP64 C with OpenMP over items")}
+                       f"({steps} path-steps in {el:.1f} s); FP64 C with OpenMP over items"),
+            "single_thread": {"value": steps1 / el1, "unit": "path-steps/s", "cores": 1,
+                              "sample": (f"the same at J={p1.J}, N1={CPU_N1} + {CPU_NPRICE // 5} "
+                                         f"pricing paths ({steps1} path-steps in {el1:.1f} s)")}}
 
 
 def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
