@@ -179,7 +179,13 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     rule = kernel_rule(o, rule);
     const void* fn = path_fn(o->d, rule, fp64);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
-    const size_t smem = path_smem_bytes(a, rule, fp64, o->d);
+    size_t smem = path_smem_bytes(a, rule, fp64, o->d);
+    if (smem > 227 * 1024 && fp64 && rule != R_NONE) {
+        // the FP64 re-run of a table too large to stage (many dates, many coefficients or
+        // stumps): its kernel reads the rule rows from global memory instead
+        a.rules_global = 1;
+        smem = path_smem_bytes(a, rule, fp64, o->d);
+    }
     if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps = 1;
     TRY(path_blocks_per_sm(fn, o->device, smem, &bps));

@@ -55,6 +55,8 @@ struct PathArgs {
     int rule_kind;
     const void* rule_src;        // staged rule table (Real), dates 0..n_dates
     int rule_stride;             // Reals per date
+    int rules_global;            // FP64 kernels only: read the rows of dates m+1.. from rule_src
+                                 // (a table too large for shared memory)
     int n_bnd, n_coef, degree;
     const int* fitted;           // n_dates + 1
     // epilogues
@@ -223,7 +225,7 @@ template <int D, typename Real> constexpr int path_min_blocks() {
 // only) and the per-date "fitted" flags.
 inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
     const size_t nk = (size_t)(a.n_dates - a.m);
-    const size_t n = (rule != R_NONE ? (nk - 1) * (size_t)a.rule_stride : 0) + nk +
+    const size_t n = (rule != R_NONE && !a.rules_global ? (nk - 1) * (size_t)a.rule_stride : 0) + nk +
                      (a.uniform ? 0 : 2 * nk * (size_t)d);
     return n * (fp64 ? 8 : 4) + nk * sizeof(int);
 }
@@ -303,7 +305,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
     constexpr int NF = D + 1;
     constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
-    const int rule_len = (RULE == R_NONE) ? 0 : (nk - 1) * a.rule_stride;   // dates m+1..NT-1
+    // rows of dates m+1..NT-1, staged in shared memory (global for an FP64 table too large)
+    const bool rules_global = sizeof(Real) == 8 && a.rules_global != 0;
+    const int rule_len = (RULE == R_NONE || rules_global) ? 0 : (nk - 1) * a.rule_stride;
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
     Real* sh_disc = sh_rule + rule_len;
     Real* sh_drift = sh_disc + nk;                   // non-uniform dates: [nk][D]
@@ -311,9 +315,12 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
     int* sh_fit = reinterpret_cast<int*>(sh_vol + (a.uniform ? 0 : nk * D));
 
     const DevModel* M = a.model;
+    const Real* rule_rows = sh_rule;
     if (RULE != R_NONE) {
         const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
         for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
+        if constexpr (sizeof(Real) == 8)
+            if (rules_global) rule_rows = src;
     }
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         const int k = a.m + 1 + i;
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
 #pragma unroll
                             for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
                             Real cc[P4];
-                            load_vec<P4>(sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
+                            load_vec<P4>(rule_rows + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
                             Real B = cc[0];
                             if constexpr (D > 1) {
                                 Real y[D - 1];
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                             Real sp = S[0];
 #pragma unroll
                             for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
-                            const Real* cc = sh_rule + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4;
+                            const Real* cc = rule_rows + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4;
                             Real B = cc[0];
                             if constexpr (D > 1) {
                                 Real y[D - 1];
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                             }
                             ex = is_put ? (sp <= B) : (sp >= B);
                     } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
-                            const Real* rec = sh_rule + kr * a.rule_stride;
+                            const Real* rec = rule_rows + kr * a.rule_stride;
                             Real F = rec[0];
 #pragma unroll
                             for (int f = 0; f < NF; ++f) {

@@ -13,8 +13,8 @@ import pytest
 import oracle
 import paper_0805_1827_gb300 as bap
 from bap_workloads import (CMCParams, IZParams, OptionSpec, PURPOSE_CMC, PURPOSE_IZ,
-                           equicorrelation, spec_max_call, spec_put_1d, workload_basket_put_7d,
-                           workload_max_call_5d)
+                           equicorrelation, spec_basket_put_7, spec_max_call, spec_put_1d,
+                           with_dates, workload_basket_put_7d, workload_max_call_5d)
 from pins import bs_price, max_call_equicorr
 from rules_io import to_buffer
 
@@ -125,6 +125,31 @@ def test_sixty_four_dates_price_matches_oracle():
     o = oracle.price(spec, rules, 200_000, 4)
     assert abs(g["price"] - o["price"]) <= 0.5 * o["se"]
     assert g["path_steps"] == pytest.approx(o["path_steps"], rel=1e-3)
+    opt.close()
+
+
+@pytest.mark.parametrize("case", ["iz_10_assets", "cmc_256_stumps"])
+def test_largest_rule_tables_fp64_rerun_matches_the_oracle(case):
+    """At 64 dates the FP64 pricing re-run's rule table outgrows shared memory (a 10-asset
+    max-call: 10 quadratic boundaries in 9 variables, 56 coefficients each; or 256 stumps over 8
+    features), so that kernel reads the rule rows from global memory.  Under the device's own
+    fitted rules the device's FP64 price, price - fp64_delta, is the oracle's price on the same
+    counters."""
+    from rules_io import from_buffer
+    if case == "iz_10_assets":
+        spec = spec_max_call(10, 100.0, rho=0.3, n_dates=64, T=2.0)
+        opt = bap.Option(spec)
+        opt.fit_boundary(IZParams(J=64, N1=128, degree=2, seed=3))
+    else:
+        spec = with_dates(spec_basket_put_7(0), 64)
+        opt = bap.Option(spec)
+        opt.fit_classifier(CMCParams(J=512, N2=64, n_stumps=256, seed=3))
+    g = opt.price(20_000, 7)
+    rules = from_buffer(opt.export_rules())
+    o = oracle.price(spec, rules, 20_000, 7, n_threads=8)
+    g64 = g["price"] - g["fp64_delta"]
+    assert abs(g64 - o["price"]) <= 0.05 * o["se"], (g64, o["price"], o["se"])
+    assert abs(g["price"] - o["price"]) <= 0.5 * o["se"]
     opt.close()
 
 
