@@ -263,18 +263,17 @@ __device__ __forceinline__ unsigned load_acquire_gpu(const unsigned* p) {
 }
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.  *bar counts block arrivals
-// over the whole launch (zero before it); barrier number g = 1, 2, ... is passed once it reaches
-// g * gridDim.x.  A block that waits longer than limit_ns, or sees *err set by another block,
-// sets *err and gets false: the caller then leaves the kernel, so every block ends in bounded
-// time and the host reads the flag.
-__device__ inline bool grid_barrier(unsigned* bar, unsigned g, int* err, unsigned long long limit_ns) {
+// over the whole launch (zero before it); a barrier is passed once the count reaches `target`,
+// the arrivals of all barriers so far (the blocks still running at each).  A block that waits
+// longer than limit_ns, or sees *err set by another block, sets *err and gets false: the caller
+// then leaves the kernel, so every block ends in bounded time and the host reads the flag.
+__device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* err, unsigned long long limit_ns) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
         __threadfence();
         atomicAdd(bar, 1u);
-        const unsigned target = g * gridDim.x;
         const unsigned long long t0 = global_ns();
         while (load_acquire_gpu(bar) < target) {
             if (*(volatile int*)err != 0 || global_ns() - t0 > limit_ns) {
@@ -358,6 +357,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
 
     int it = COOP ? 0 : (a.iter_ptr ? *a.iter_ptr : a.pass_it);
     bool ok = true;
+    // cooperative form: the blocks that run the current pass (0 .. active-1), and the barrier
+    // count that ends it
+    unsigned active = gridDim.x, bar_target = 0;
     for (;;) {
     // ---- one pass: every unit of the count[it] items of list[it & 1] ----
     const long long total_units = (long long)__ldcg(a.count + it) * a.C;
@@ -663,8 +665,16 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             }
         }
     if constexpr (!COOP) break;
-    ok = grid_barrier(a.coop_bar, (unsigned)(it + 1), a.coop_err, a.coop_limit_ns);
-    if (!ok || __ldcg(a.count + it + 1) == 0 || it + 1 >= a.max_iter) break;
+    bar_target += active;
+    ok = grid_barrier(a.coop_bar, bar_target, a.coop_err, a.coop_limit_ns);
+    if (!ok) break;
+    const int next_count = __ldcg(a.count + it + 1);
+    if (next_count == 0 || it + 1 >= a.max_iter) break;
+    // blocks beyond what the next pass's units can occupy leave, so that their SMs serve other
+    // work (every block reads the same count, so all agree on who stays)
+    const long long need = ((long long)next_count * a.C + (blockDim.x / 32) - 1) / (blockDim.x / 32);
+    if (need < (long long)active) active = (unsigned)need;
+    if (blockIdx.x >= active) break;
     ++it;
     }
     if (COOP && ok && blockIdx.x == 0 && threadIdx.x == 0 && a.passes) *a.passes += it + 1;
