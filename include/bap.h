@@ -303,7 +303,7 @@ bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_
 bap_status bap_server_create(size_t device_mem_budget, int max_inflight, bap_server **out);
 
 /* Launch form of the I&Z fits the server runs (see bap_set_launch_mode).  Default 2 (one
- * cooperative launch per date, on at most 1/min(max_inflight, 4) of the device): each request
+ * cooperative launch per date, on at most 1/min(max_inflight, 8) of the device): each request
  * builds its fit once, so a graph's build and release cost more host time than its launches
  * save, and the plain form's max_iter launches per date fill the stream's launch queue. */
 bap_status bap_server_set_launch_mode(bap_server *srv, int mode);

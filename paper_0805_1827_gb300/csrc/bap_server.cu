@@ -86,7 +86,10 @@ bool start_request(bap_server* s, Request* r) {
     const auto t1 = Clock::now();
     if (st == BAP_OK) {
         r->opt->launch_mode = s->launch_mode;
-        r->opt->grid_share = std::min(s->max_inflight, 4);
+        // cooperative launches on at most an eighth of the device each (measured best on the
+        // mixed stream once idle blocks leave between passes: a quarter 79.2, a half 65.2,
+        // an eighth 81.2 options/s)
+        r->opt->grid_share = std::min(s->max_inflight, 8);
     }
     if (st == BAP_OK)
         st = r->method == BAP_METHOD_IZ ? enqueue_fit_iz(r->opt, &r->iz) : enqueue_fit_cmc(r->opt, &r->cmc);
