@@ -172,3 +172,23 @@ def test_adaboost_constant_labels_stop_after_one_perfect_stump():
     assert len(st) == 1
     f, thr, pol, a = st[0]
     assert thr == -math.inf and pol == -1 and a > 10
+
+
+def test_adaboost_normalised_step_has_a_closed_form():
+    """AdaBoost's step w <- w exp(-alpha y h) / Z with alpha = 1/2 ln((1 - eps) / eps) leaves the
+    points the stump classifies right with half of the weight, so it equals w / (2 (1 - eps)) on
+    those and w / (2 eps) on the others: the form the device uses, in which no sum enters."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        n = int(rng.integers(5, 400))
+        w = rng.random(n) ** 3
+        w /= w.sum()
+        right = rng.random(n) < rng.uniform(0.55, 0.99)
+        right[0], right[1] = True, False
+        eps = w[~right].sum()
+        alpha = 0.5 * math.log((1.0 - eps) / eps)
+        textbook = w * np.exp(np.where(right, -alpha, alpha))
+        textbook /= textbook.sum()
+        closed = np.where(right, w / (2.0 * (1.0 - eps)), w / (2.0 * eps))
+        assert np.allclose(textbook, closed, rtol=1e-13, atol=0.0)
+        assert textbook[right].sum() == pytest.approx(0.5, rel=1e-13)

@@ -77,3 +77,31 @@ def test_cmc_with_logitboost_prices_like_adaboost():
         res[boost] = oracle.price(spec, rules, 200_000, seed=3, n_threads=4)
     a, b = res[0], res[1]
     assert abs(a["price"] - b["price"]) < 4 * np.hypot(a["se"], b["se"]) + 0.02
+
+
+def test_fp32_split_gain_is_within_the_prefilter_bound():
+    """The device screens LogitBoost's splits with the gain S_L^2/W_L + S_R^2/W_R taken in FP32
+    from the 2^48 fixed-point sums (four conversions, two squares, two divisions, an add, each
+    correctly rounded) and keeps every split within a relative 8e-6 of the block's largest FP32
+    gain.  That is safe if the FP32 gain is within a relative 4e-7 of the exact one; checked here
+    on sums of the sizes a fit produces (W up to 2^58, |S| <= 4 W, any split)."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(20000):
+        W = int(rng.integers(2 ** 20, 2 ** 58))
+        S = int(rng.integers(-4 * W, 4 * W))
+        WL = int(rng.integers(1, W))
+        # S_L within the weights it sums: |S_L| <= 4 W_L and |S - S_L| <= 4 (W - W_L)
+        lo = max(-4 * WL, S - 4 * (W - WL))
+        hi = min(4 * WL, S + 4 * (W - WL))
+        if lo > hi:
+            continue
+        SL = int(rng.integers(lo, hi + 1))
+        f32 = np.float32
+        a, b = f32(WL), f32(SL)
+        ra, sb = f32(W - WL), f32(S - SL)
+        g32 = float(b * b / a + sb * sb / ra)
+        exact = (SL * SL) / WL + ((S - SL) * (S - SL)) / (W - WL)   # float of exact rationals
+        if exact > 0:
+            worst = max(worst, abs(g32 - exact) / exact)
+    assert worst < 4e-7, worst
