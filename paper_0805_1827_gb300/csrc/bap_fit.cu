@@ -581,11 +581,13 @@ __global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int*
 // candidate with error <= e_min + 1e-12 wins.  alpha = 1/2 ln((1-eps)/eps) with eps clamped to
 // [1e-10, 1-1e-10]; stop before a stump with eps >= 1/2 and after a perfect one.
 //
-// The weights are FP64 and normalised every round; the weighted errors are summed exactly in
-// 64-bit fixed point (w 2^60, integer adds on the full-rate ALU instead of the narrow FP64
-// pipe), as one block-wide prefix scan per feature over contiguous segments of the sorted
-// order.  The update multiplies each weight by exp(-alpha) or exp(+alpha), the two values
-// exp(-alpha y h) takes.
+// The weights are FP64; the weighted errors are summed exactly in 64-bit fixed point (w 2^60,
+// integer adds on the full-rate ALU instead of the narrow FP64 pipe), as one block-wide prefix
+// scan per feature over contiguous segments of the sorted order.  The update is the closed form
+// of the normalised step w exp(-alpha y h) / Z: w / (2 (1 - eps)) for a point the stump
+// classifies right, w / (2 eps) for one it gets wrong (with that alpha the right points keep
+// half of the weight).  No sum enters it, so every form of the fit gives the same weights; the
+// three quotients are taken on three warps, and alpha's log once per stump at the end.
 
 constexpr double kFix = 1152921504606846976.0;   // 2^60
 
@@ -922,8 +924,8 @@ __global__ void __launch_bounds__(1024) adaboost_kernel(
 // ---------------------------------------------------------------------------------------------
 // [class] The same AdaBoost fit on a thread-block cluster: block f (cluster rank f) owns feature
 // f, so the per-feature sorts, prefix scans and error searches of a round run on nF SMs at once.
-// Every block keeps its own copy of the weights and applies the same update in the same order,
-// so the copies stay identical.  Per round the blocks exchange, through the distributed shared
+// Every block keeps its own copy of the weights and applies the same update, so the copies
+// stay identical.  Per round the blocks exchange, through the distributed shared
 // memory of the leader block (rank 0): the least error of each feature, then the first
 // candidate of each feature within the tolerance and its error and threshold.  Two cluster
 // barriers per round; every decision is taken from values read back from the leader, so all
@@ -1185,9 +1187,8 @@ __global__ void __launch_bounds__(kClusterBoostThreads) adaboost_cluster_kernel(
 // largest prefix at a split.  Those give the feature's least error, min(neg + min S,
 // W - neg - max S), and, once the round's least error is known, the first segment holding a
 // candidate, which the whole warp rescans.  Choices, tie rule and weight update are those of
-// adaboost_cluster_kernel, the update in the same thread layout and summation order, so the
-// stumps are the cluster form's bit for bit; the FP64 division, log and exp of a round run on
-// one thread.
+// adaboost_cluster_kernel, so the stumps are the cluster form's bit for bit; the round's three
+// FP64 quotients run on three warps and the thresholds and logs once per stump at the end.
 
 // Storage index of sorted position r (and, the map being its own inverse, the position held at
 // storage index r): the two 5-bit fields below bit 10 swapped.
@@ -1472,8 +1473,9 @@ __global__ void __launch_bounds__(kWarpBoostThreads) adaboost_warp_kernel(
 // least-squares gain S_L^2 / W_L + S_R^2 / W_R over the splits between distinct sorted values
 // (no split: S^2 / W), the first within a relative 1e-12 of the largest in (no split, feature,
 // threshold) order; leaves c = S / W; F <- F + f / 2.  The sums of w and w z are exact in 2^48
-// fixed point.  The FP64 exp of p is the costly part: block f computes it for its own slice of
-// the points and the blocks gather each other's slices through distributed shared memory.  A
+// fixed point.  Block f computes p, w and z (an FP64 exp each) for its own slice of the points
+// and the blocks gather each other's slices through distributed shared memory; split gains are
+// screened in FP32 and taken exactly in FP64 only near the largest (see below).  A
 // round is stored as two vote stumps (threshold stump |B|, constant |A|; A = (c_L + c_R) / 4,
 // B = (c_R - c_L) / 4), so the rule staging and the path kernel are the AdaBoost ones.
 
