@@ -88,7 +88,9 @@ typedef struct bap_iz_params {
     double f_tol;             /* stop when |Phi(x) - C(x)| < f_tol (e.g. 1e-6) */
     double x_tol;             /* or when the step or bracket is <= x_tol * max(1, |x|) (e.g. 1e-5) */
     int max_iter;             /* Newton iterations per point, 1..200 (e.g. 50) */
-    int degree;               /* boundary polynomial degree 0..2 (d = 1 uses 0) */
+    int degree;               /* boundary polynomial degree 0..3 in the d-1 other assets
+                                 (Section 2.1: linear, quadratic or cubic; 3 needs d <= 6;
+                                 d = 1 uses 0) */
     uint64_t seed;
     int fixed_point;          /* 1: the paper's literal iteration x <- Phi^-1(C(x)) with |dx| <
                                  fp_eps (Section 2.4); 0: safeguarded Newton */
@@ -161,8 +163,9 @@ typedef struct bap_server_stats {
 typedef struct bap_option bap_option;
 typedef struct bap_server bap_server;
 
-/* Create an option: copies and validates the model (FP64 Cholesky of rho on the device) and
- * uploads it.  *out is set on success.  Errors: EINVAL (bad model), ENOMEM, ECUDA. */
+/* Create an option: copies and validates the model (an FP64 Cholesky factorisation of rho on
+ * the host checks that it is positive definite) and uploads it with the per-date stepping
+ * constants.  *out is set on success.  Errors: EINVAL (bad model), ENOMEM, ECUDA. */
 bap_status bap_create(const bap_model *model, bap_option **out);
 
 /* Run the option's work on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream). */
@@ -257,6 +260,43 @@ bap_status bap_debug_continuation(bap_option *opt, int m, int purpose, uint64_t 
 bap_status bap_debug_paths(bap_option *opt, int m, int purpose, uint64_t seed, int item_id,
                            const double *start, int64_t N, int *tau, double *disc_phi);
 
+/* One date of the I&Z fit's Newton loop ([calc], Section 2.3) for caller-given boundary points,
+ * under the option's current rules for the later dates (parity hook: with rules imported by
+ * bap_import_rules, the points can be compared with another implementation's on the same
+ * rules).  Item i starts from starts[i*d..] (the pivot coordinate pivots[i] in 0..d-1 is
+ * replaced by the initial iterate, chosen as in the fit; the others must be positive) and uses
+ * Philox counter word item_ids[i]; warm_start reads the option's boundary of date m+1.  The
+ * launch form is the option's (cooperative, else one launch per pass) with the fit's work split
+ * for n_items items and params->N1 paths.  Outputs per item: the final point x, the number of
+ * continuation evaluations, the status (0 ok, 1 no convergence, 2 no root) and, if lo and hi
+ * are not NULL, the final bracket of the safeguarded Newton iteration (an end not yet found is
+ * 0 or +infinity); *path_steps (may be NULL) = inner path-steps taken.  The option's fit scratch
+ * is reused (its fit diagnostics and rules are kept).  Errors: EINVAL, ESTATE (the option holds
+ * a CMC rule), ECUDA. */
+bap_status bap_debug_newton(bap_option *opt, const bap_iz_params *params, int m, int n_items,
+                            const int *item_ids, const int *pivots, const double *starts,
+                            double *x, int *iters, int *status, double *lo, double *hi,
+                            int64_t *path_steps);
+
+/* The I&Z least-squares boundary fit ([reg], Section 2.2) of one date on caller-given points
+ * (parity hook).  n_bnd = d for the max-call with d > 1, else 1; boundary b holds points
+ * b*J .. b*J+J-1: starts[(b*J+j)*d..] (the other assets' values; the pivot's entry is ignored),
+ * x[b*J+j] the point along the pivot and status[b*J+j] (2 = no root: left out).  coef receives
+ * n_bnd x n_basis(d-1, degree) FP64 coefficients of x/K in the monomials of y/K, in the order
+ * [1, y_a, y_a y_b (a <= b), y_a y_b y_c (a <= b <= c)], exactly as bap_export_rules stores a
+ * date.  The option's rules are not touched.  Errors: EINVAL, ECUDA. */
+bap_status bap_debug_ls_fit(bap_option *opt, int degree, int J, const double *starts,
+                            const double *x, const int *status, double *coef);
+
+/* The CMC boosting of one date ([class], Section 3.2) on caller-given training points X (J x d,
+ * positive) and labels (+1 exercise / -1 continue), in the option's boosting form (parity hook).
+ * The stumps become the option's rule of date m (if the option does not hold a CMC rule with
+ * room for params->n_stumps stumps, or twice that for LogitBoost, an empty one is set up
+ * first).  *n_stumps = stumps fitted; stumps receives max_stumps x (feature, threshold,
+ * polarity, alpha), the layout of bap_export_rules.  Errors: EINVAL, ECUDA. */
+bap_status bap_debug_boost(bap_option *opt, const bap_cmc_params *params, int m, const double *X,
+                           const int *labels, int *n_stumps, double *stumps);
+
 /* Continuation sums that allocate no device memory.  The paper has no counterpart to this call.
  * It is for callers that cannot allocate device memory while they run -- code inside a host
  * framework whose allocator owns all of the GPU's memory, or a latency-bound loop that must not
@@ -264,13 +304,20 @@ bap_status bap_debug_paths(bap_option *opt, int m, int purpose, uint64_t seed, i
  * device buffers.  It computes what bap_debug_continuation computes, but:
  *   - every array is a DEVICE pointer: d_item_ids and d_pivots (n_items ints; d_pivots may be
  *     NULL), d_starts (n_items*d doubles), d_sums (n_items*3 doubles), d_steps (n_items);
- *   - the call only enqueues work on the option's stream and returns; synchronize that stream
- *     before reading d_sums and d_steps;
+ *   - a pivot must lie in -1..d-1 and every start coordinate must be positive.  The inputs are
+ *     checked on the device: an item that breaks either rule gets NaN sums and steps = -1 (its
+ *     pivot is treated as -1, so no access leaves the caller's buffers); the other items are
+ *     unaffected.  The call itself cannot see the device data and returns OK;
+ *   - the call only enqueues work on the option's stream and returns.  The inputs must be
+ *     complete with respect to that stream when the call is made: if they were written on
+ *     another stream, synchronize it or make the option's stream wait on an event first.
+ *     Synchronize the option's stream before reading d_sums and d_steps;
  *   - its scratch is a fixed 4 MiB array in the library's device image (one per GPU that loads
  *     the library, held until the process exits).  A call needs about 32 bytes per
  *     (item, unit of up to 2048 paths) plus 4 bytes per item; larger calls return BAP_EINVAL;
- *   - the first call on a device looks up the array's address (that device must be current, as
- *     for every call on the option); make that first call before any stream capture;
+ *   - every call looks up the array's address on the current device (which must be the
+ *     option's, as for every call on the option); the first lookup on a device may load the
+ *     library's device image there, so make the first call before any stream capture;
  *   - all calls share the array, and it keeps the last call's contents (the call clears what it
  *     needs zeroed): calls whose work overlaps on the GPU -- on different streams, or different
  *     options on one device -- race on it and corrupt each other's sums.  Serialize them. */

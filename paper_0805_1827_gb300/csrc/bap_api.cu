@@ -1,9 +1,10 @@
 // bap_api.cu -- host side of the C ABI declared in include/bap.h.
 //
 // The host validates arguments, owns device buffers and enqueues kernels on the option's
-// stream.  Every step of the method (Cholesky, lattice, Newton iterations, regression,
-// training points, boosting, pricing) runs in device kernels; the host reads back only the
-// results a call returns.  Fits and pricing are split into an enqueue part (asynchronous on the
+// stream.  The FP64 Cholesky factorisation of rho (a few hundred flops per option, the
+// positive-definiteness check) runs on the host when the option is created; every other step
+// of the method (lattice, Newton iterations, regression, training points, boosting, pricing)
+// runs in device kernels, and the host reads back only the results a call returns.  Fits and pricing are split into an enqueue part (asynchronous on the
 // option's stream, results into page-locked host memory) and a finish part, so that the serving
 // loop can keep many options in flight.
 #include <algorithm>
@@ -175,7 +176,9 @@ int kernel_rule(const bap_option* o, int rule) {
     return rule;
 }
 
-bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units) {
+// no_events: never create profiling events (the allocation-free entry point creates nothing).
+bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units,
+                       bool no_events = false) {
     rule = kernel_rule(o, rule);
     const void* fn = path_fn(o->d, rule, fp64);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
@@ -196,7 +199,7 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     blocks = std::max(1LL, std::min(blocks, cap));
     void* args[] = {&a};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool timed = o->profiling && !fp64 && !o->capturing;
+    const bool timed = o->profiling && !fp64 && !o->capturing && !no_events;
     if (timed) {
         while (o->prof_ev.size() < o->prof_used + 2) {
             cudaEvent_t e;
@@ -1047,6 +1050,109 @@ bap_status boost_cluster_fits(const void* fn, int device, int nF, size_t smem, i
     return BAP_OK;
 }
 
+// How the boosting of a J-point CMC date runs: the kernel form and its shared memory.
+struct BoostPlan {
+    bool logit = false, warp_form = false, cluster = false;
+    int cl_threads = 0;
+    size_t ab_smem = 0, abc_smem = 0, abw_smem = 0, lb_smem = 0;
+};
+
+bap_status boost_plan(bap_option* o, const bap_cmc_params* p, BoostPlan* bp) {
+    const int J = p->J, nF = o->d + 1;
+    cudaStream_t st = o->stream;
+    BoostPlan& b = *bp;
+    b.logit = p->boost == 1;
+    int P2 = 1;
+    while (P2 < J) P2 <<= 1;
+    b.ab_smem = (size_t)J * 8 + std::max((size_t)P2 * 12, (size_t)J * 8) + (size_t)J + 16;
+    // the cluster form (one block per feature) when asked for and the device can place it
+    b.abc_smem = (size_t)J * 10 + std::max((size_t)P2 * 12, (size_t)J * 16) + 4 +
+                 8 * (size_t)((J + 31) / 32);
+    b.cl_threads = cluster_boost_threads(J);
+    // LogitBoost: one cluster of nF blocks (the slices of F, the sums, both permutations)
+    const size_t ns_lb = (size_t)((J + nF - 1) / nF);
+    b.lb_smem = ns_lb * 8 + std::max((size_t)P2 * 12, (size_t)J * 24) + 2 * (size_t)J + 4 +
+                4 * (size_t)((J + 31) / 32);
+    if (b.logit) {
+        TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, b.lb_smem, b.cl_threads, st, &b.cluster));
+        if (!b.cluster)
+            return fail(BAP_EINVAL, "LogitBoost needs a cluster of %d blocks with %zu B of shared memory each", nF, b.lb_smem);
+    }
+    // AdaBoost: the warp-per-feature block (form 2; by default only up to J = 2048, above which
+    // the cluster's per-block scans are shorter) when its shared memory fits, else the cluster
+    // (form 1) when the device can place it, else the one-block form
+    b.abw_smem = warp_boost_smem(J, nF);
+    {
+        std::lock_guard<std::mutex> lk(g_fn_mu);
+        TRY(raise_smem_limit((const void*)adaboost_kernel, o->device, g_fn[{(const void*)adaboost_kernel, o->device}]));
+        FnInfo& fw = g_fn[{(const void*)adaboost_warp_kernel, o->device}];
+        TRY(raise_smem_limit((const void*)adaboost_warp_kernel, o->device, fw));
+        const bool want_warp = o->boost_form == 2 || (o->boost_form == 3 && J <= kWarpBoostAutoMaxJ);
+        b.warp_form = !b.logit && want_warp && b.abw_smem <= fw.max_dyn_smem;
+    }
+    if (!b.logit && !b.warp_form && o->boost_form >= 1)
+        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, b.abc_smem, b.cl_threads, st, &b.cluster));
+    o->last_boost_form = b.logit ? 1 : b.warp_form ? 2 : b.cluster ? 1 : 0;
+    return BAP_OK;
+}
+
+// The boosting of date m ([class]) on the J points in o->start and their labels in o->label;
+// the stumps become the rule of date m.
+bap_status enqueue_boost(bap_option* o, const BoostPlan& b, const bap_cmc_params* p, int m) {
+    const int J = p->J, nF = o->d + 1;
+    cudaStream_t st = o->stream;
+    if (b.logit) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        boost_cluster_config(cfg, attr, nF, b.lb_smem, st, b.cl_threads);
+        CU(cudaLaunchKernelEx(&cfg, logitboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
+                              m, J, (const double*)o->start.as<double>(),
+                              (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
+                              o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
+                              o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+                              o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
+                              o->rec_d.as<double>(), o->fitted.as<int>()));
+    } else if (b.warp_form) {
+        adaboost_warp_kernel<<<1, kWarpBoostThreads, b.abw_smem, st>>>(
+            o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label.as<int>(),
+            p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(), o->max_stumps,
+            o->n_stumps.as<int>(), o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+            o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(), o->rec_d.as<double>(),
+            o->fitted.as<int>());
+    } else if (b.cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        boost_cluster_config(cfg, attr, nF, b.abc_smem, st, b.cl_threads);
+        CU(cudaLaunchKernelEx(&cfg, adaboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
+                              m, J, (const double*)o->start.as<double>(),
+                              (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
+                              o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
+                              o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
+                              o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
+                              o->rec_d.as<double>(), o->fitted.as<int>()));
+    } else {
+        adaboost_kernel<<<1, 1024, b.ab_smem, st>>>(
+            o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label_y.as<double>(),
+            o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(),
+            o->err.as<double>(), o->max_stumps, o->n_stumps.as<int>(), o->feat.as<int>(),
+            o->thr.as<double>(), o->pol.as<int>(), o->alpha.as<double>(), o->rec_len,
+            o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
+    }
+    ++o->launches;
+    const cudaError_t eb = cudaGetLastError();
+    if (eb != cudaSuccess) return fail(BAP_ECUDA, "boosting launch: %s", cudaGetErrorString(eb));
+    return BAP_OK;
+}
+
+// Buffers of the boosting of J points over d+1 features.
+bap_status reserve_boost(bap_option* o, int J) {
+    const int nF = o->d + 1;
+    TRY(o->sorted_v.reserve((size_t)nF * J * 8));
+    TRY(o->sorted_i.reserve((size_t)nF * J * 4));
+    TRY(o->err.reserve((size_t)nF * J * 8));
+    return BAP_OK;
+}
+
 bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     AllocScope scope(o->stream);
     o->launches = o->path_launches = 0;
@@ -1068,11 +1174,9 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     o->n_items = n;
     const int chunk = choose_chunk(n, p->N2);
     const int C = (int)((p->N2 + chunk - 1) / chunk);
-    const int d = o->d, nF = d + 1;
+    const int d = o->d;
     TRY(reserve_items(o, n, C, 1));
-    TRY(o->sorted_v.reserve((size_t)nF * J * 8));
-    TRY(o->sorted_i.reserve((size_t)nF * J * 4));
-    TRY(o->err.reserve((size_t)nF * J * 8));
+    TRY(reserve_boost(o, J));
     if (p->sampler == 1) TRY(o->bridge_w.reserve((size_t)J * d * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
     TRY(o->diag_it.reserve((size_t)(o->n_dates + 1) * n * 4));
@@ -1083,39 +1187,8 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     CU(cudaMemsetAsync(o->done.p, 0, (size_t)n * 4, st));
     CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
     CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
-    int P2 = 1;
-    while (P2 < J) P2 <<= 1;
-    const size_t ab_smem = (size_t)J * 8 + std::max((size_t)P2 * 12, (size_t)J * 8) + (size_t)J + 16;
-    // the cluster form (one block per feature) when asked for and the device can place it
-    const size_t abc_smem = (size_t)J * 10 + std::max((size_t)P2 * 12, (size_t)J * 16) + 4 +
-                            8 * (size_t)((J + 31) / 32);
-    bool cluster = false;
-    const int cl_threads = cluster_boost_threads(J);
-    // LogitBoost: one cluster of nF blocks (the slices of F, the sums, both permutations)
-    const size_t ns_lb = (size_t)((J + nF - 1) / nF);
-    const size_t lb_smem = ns_lb * 8 + std::max((size_t)P2 * 12, (size_t)J * 24) + 2 * (size_t)J + 4 +
-                           4 * (size_t)((J + 31) / 32);
-    if (logit) {
-        TRY(boost_cluster_fits((const void*)logitboost_cluster_kernel, o->device, nF, lb_smem, cl_threads, st, &cluster));
-        if (!cluster)
-            return fail(BAP_EINVAL, "LogitBoost needs a cluster of %d blocks with %zu B of shared memory each", nF, lb_smem);
-    }
-    // AdaBoost: the warp-per-feature block (form 2; by default only up to J = 2048, above which
-    // the cluster's per-block scans are shorter) when its shared memory fits, else the cluster
-    // (form 1) when the device can place it, else the one-block form
-    const size_t abw_smem = warp_boost_smem(J, nF);
-    bool warp_form = false;
-    {
-        std::lock_guard<std::mutex> lk(g_fn_mu);
-        TRY(raise_smem_limit((const void*)adaboost_kernel, o->device, g_fn[{(const void*)adaboost_kernel, o->device}]));
-        FnInfo& fw = g_fn[{(const void*)adaboost_warp_kernel, o->device}];
-        TRY(raise_smem_limit((const void*)adaboost_warp_kernel, o->device, fw));
-        const bool want_warp = o->boost_form == 2 || (o->boost_form == 3 && J <= kWarpBoostAutoMaxJ);
-        warp_form = !logit && want_warp && abw_smem <= fw.max_dyn_smem;
-    }
-    if (!logit && !warp_form && o->boost_form >= 1)
-        TRY(boost_cluster_fits((const void*)adaboost_cluster_kernel, o->device, nF, abc_smem, cl_threads, st, &cluster));
-    o->last_boost_form = logit ? 1 : warp_form ? 2 : cluster ? 1 : 0;
+    BoostPlan bp;
+    TRY(boost_plan(o, p, &bp));
     CU(cudaEventRecord(o->ev0, st));
     for (int m = o->n_dates - 1; m >= 1; --m) {
         const int ph_calc = phase_begin(o, PH_CALC);
@@ -1148,48 +1221,10 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
         phase_end(o, ph_calc);
         TRY(sl);
         const int ph_fit = phase_begin(o, PH_FIT);
-        if (logit) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            boost_cluster_config(cfg, attr, nF, lb_smem, st, cl_threads);
-            CU(cudaLaunchKernelEx(&cfg, logitboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
-                                  m, J, (const double*)o->start.as<double>(),
-                                  (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
-                                  o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
-                                  o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
-                                  o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
-                                  o->rec_d.as<double>(), o->fitted.as<int>()));
-        } else if (warp_form) {
-            adaboost_warp_kernel<<<1, kWarpBoostThreads, abw_smem, st>>>(
-                o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label.as<int>(),
-                p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(), o->max_stumps,
-                o->n_stumps.as<int>(), o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
-                o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(), o->rec_d.as<double>(),
-                o->fitted.as<int>());
-        } else if (cluster) {
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            boost_cluster_config(cfg, attr, nF, abc_smem, st, cl_threads);
-            CU(cudaLaunchKernelEx(&cfg, adaboost_cluster_kernel, (const DevModel*)o->dmodel.as<DevModel>(),
-                                  m, J, (const double*)o->start.as<double>(),
-                                  (const int*)o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(),
-                                  o->sorted_i.as<int>(), o->max_stumps, o->n_stumps.as<int>(),
-                                  o->feat.as<int>(), o->thr.as<double>(), o->pol.as<int>(),
-                                  o->alpha.as<double>(), o->rec_len, o->rec_f.as<float>(),
-                                  o->rec_d.as<double>(), o->fitted.as<int>()));
-        } else {
-            adaboost_kernel<<<1, 1024, ab_smem, st>>>(
-                o->dmodel.as<DevModel>(), m, J, o->start.as<double>(), o->label_y.as<double>(),
-                o->label.as<int>(), p->n_stumps, o->sorted_v.as<double>(), o->sorted_i.as<int>(),
-                o->err.as<double>(), o->max_stumps, o->n_stumps.as<int>(), o->feat.as<int>(),
-                o->thr.as<double>(), o->pol.as<int>(), o->alpha.as<double>(), o->rec_len,
-                o->rec_f.as<float>(), o->rec_d.as<double>(), o->fitted.as<int>());
-        }
-        ++o->launches;
-        const cudaError_t eb = cudaGetLastError();
-        const bap_status sd = eb == cudaSuccess ? record_diag(o, m, false) : BAP_OK;
+        const bap_status sb = enqueue_boost(o, bp, p, m);
+        const bap_status sd = sb == BAP_OK ? record_diag(o, m, false) : BAP_OK;
         phase_end(o, ph_fit);
-        if (eb != cudaSuccess) return fail(BAP_ECUDA, "boosting launch: %s", cudaGetErrorString(eb));
+        TRY(sb);
         TRY(sd);
     }
     CU(cudaEventRecord(o->ev1, st));
@@ -1440,6 +1475,167 @@ bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int
     return BAP_OK;
 }
 
+bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_items,
+                            const int* item_ids, const int* pivots, const double* starts,
+                            double* x, int* iters, int* status, double* lo, double* hi,
+                            int64_t* path_steps) {
+    clear_error();
+    if (!o || !p || !item_ids || !pivots || !starts || !x || !iters || !status)
+        return fail(BAP_EINVAL, "null argument");
+    TRY(validate_iz(o->d, p));
+    if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
+    if (n_items < 1 || n_items > (1 << 24)) return fail(BAP_EINVAL, "n_items outside 1..2^24");
+    if (o->rule_kind == R_CMC) return fail(BAP_ESTATE, "the option holds a CMC rule, not boundaries");
+    const int d = o->d;
+    for (int i = 0; i < n_items; ++i) {
+        if (pivots[i] < 0 || pivots[i] >= d) return fail(BAP_EINVAL, "pivot outside 0..d-1");
+        for (int q = 0; q < d; ++q)
+            if (q != pivots[i] && !(starts[(size_t)i * d + q] > 0))
+                return fail(BAP_EINVAL, "start points must be positive");
+    }
+    AllocScope scope(o->stream);
+    cudaStream_t st = o->stream;
+    const int n_bnd = (o->payoff == BAP_MAX_CALL && d > 1) ? d : 1;
+    const int chunk = choose_chunk(n_items, p->N1);
+    const int C = (int)((p->N1 + chunk - 1) / chunk);
+    TRY(reserve_items(o, n_items, C, p->max_iter));
+    DevBuf ds, dp, di, dl;
+    TRY(ds.reserve((size_t)n_items * d * 8));
+    TRY(dp.reserve((size_t)n_items * 4));
+    TRY(di.reserve((size_t)n_items * 4));
+    TRY(dl.reserve((size_t)n_items * 4));
+    CU(cudaMemcpyAsync(ds.p, starts, (size_t)n_items * d * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dp.p, pivots, (size_t)n_items * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(di.p, item_ids, (size_t)n_items * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(o->done.p, 0, (size_t)n_items * 4, st));
+    CU(cudaMemsetAsync(o->total_steps.p, 0, 8, st));
+    CU(cudaMemsetAsync(o->stat_counts.p, 0, 16, st));
+    CU(cudaMemsetAsync(o->counts.p, 0, (size_t)(p->max_iter + 2) * 4, st));
+    CU(cudaMemsetAsync(o->work.p, 0, (size_t)(p->max_iter + 2) * 8, st));
+    const bool warm = p->warm_start && o->rule_kind == R_IZ;
+    newton_items_setup_kernel<<<(n_items + 127) / 128, 128, 0, st>>>(
+        o->dmodel.as<DevModel>(), m, n_items, n_bnd, ds.as<double>(), dp.as<int>(), di.as<int>(),
+        o->start.as<double>(), o->state.as<ItemState>(), o->pivot.as<int>(), o->ctr_item.as<int>(),
+        dl.as<int>(), warm ? o->coef64.as<double>() : nullptr, o->n_coef, o->degree,
+        o->fitted.as<int>(), warm ? 1 : 0);
+    newton_items_list_kernel<<<1, 32, 0, st>>>(dl.as<int>(), n_items, o->active0.as<int>(), o->counts.as<int>());
+    CU(cudaGetLastError());
+    // the fit's own Newton launches, on these items (the option's fit diagnostics stay as they are)
+    const int saved_n = o->n_items;
+    o->n_items = n_items;
+    bap_status sn = BAP_OK;
+    if (o->launch_mode == LAUNCH_COOP) {
+        sn = enqueue_newton_coop(o, p, m, chunk, C);
+    } else {
+        for (int it = 0; it < p->max_iter && sn == BAP_OK; ++it)
+            sn = enqueue_newton_pass(o, p, m, it, chunk, C);
+    }
+    o->n_items = saved_n;
+    TRY(sn);
+    std::vector<ItemState> hs(n_items);
+    int flags[4] = {0, 0, 0, 0};
+    unsigned long long steps = 0;
+    CU(cudaMemcpyAsync(hs.data(), o->state.p, (size_t)n_items * sizeof(ItemState), cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(flags, o->stat_counts.p, 16, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&steps, o->total_steps.p, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (flags[3] != 0) return fail(BAP_ECUDA, "Newton loop: a grid barrier of the cooperative launch timed out");
+    for (int i = 0; i < n_items; ++i) {
+        x[i] = hs[i].x;
+        iters[i] = hs[i].iters;
+        status[i] = hs[i].status;
+        if (lo) lo[i] = hs[i].lo;
+        if (hi) hi[i] = hs[i].hi;
+    }
+    if (path_steps) *path_steps = (int64_t)steps;
+    return BAP_OK;
+}
+
+bap_status bap_debug_ls_fit(bap_option* o, int degree, int J, const double* starts,
+                            const double* x, const int* status, double* coef) {
+    clear_error();
+    if (!o || !starts || !x || !status || !coef) return fail(BAP_EINVAL, "null argument");
+    const int d = o->d, s = d - 1;
+    if (s == 0) degree = 0;
+    if (degree < 0 || degree > 3 || (degree == 3 && d > MAXD_CUBIC)) return fail(BAP_EINVAL, "bad degree");
+    if (J < 1 || J > 8192) return fail(BAP_EINVAL, "J outside 1..8192");
+    const int n_bnd = (o->payoff == BAP_MAX_CALL && d > 1) ? d : 1;
+    const int n = n_bnd * J;
+    const int P = n_basis(s, degree);
+    for (int i = 0; i < n; ++i)
+        if (status[i] < 0 || status[i] > 2) return fail(BAP_EINVAL, "status outside 0..2");
+    AllocScope scope(o->stream);
+    cudaStream_t st = o->stream;
+    std::vector<ItemState> hs(n);
+    for (int i = 0; i < n; ++i) {
+        memset(&hs[i], 0, sizeof(ItemState));
+        hs[i].x = x[i];
+        hs[i].status = status[i];
+    }
+    DevBuf ds, dst, dc, dcf, dcd, dfit;
+    TRY(ds.reserve((size_t)n * d * 8));
+    TRY(dst.reserve((size_t)n * sizeof(ItemState)));
+    TRY(dc.reserve((size_t)n_bnd * P * 8));
+    TRY(dcf.reserve((size_t)n_bnd * iz_stride(d, degree) * 4));
+    TRY(dcd.reserve((size_t)n_bnd * iz_stride(d, degree) * 8));
+    TRY(dfit.reserve(16));
+    CU(cudaMemcpyAsync(ds.p, starts, (size_t)n * d * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(dst.p, hs.data(), (size_t)n * sizeof(ItemState), cudaMemcpyHostToDevice, st));
+    ls_fit_kernel<<<n_bnd, kLsThreads, 0, st>>>(o->dmodel.as<DevModel>(), 0, J, n_bnd, degree, P,
+                                                ds.as<double>(), dst.as<ItemState>(), dc.as<double>(),
+                                                dcf.as<float>(), dcd.as<double>(), dfit.as<int>());
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(coef, dc.p, (size_t)n_bnd * P * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return BAP_OK;
+}
+
+bap_status bap_debug_boost(bap_option* o, const bap_cmc_params* p, int m, const double* X,
+                           const int* labels, int* n_stumps, double* stumps) {
+    clear_error();
+    if (!o || !p || !X || !labels || !n_stumps || !stumps) return fail(BAP_EINVAL, "null argument");
+    TRY(validate_cmc(o, p));
+    if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
+    const int d = o->d, J = p->J;
+    for (int j = 0; j < J; ++j) {
+        if (labels[j] != 1 && labels[j] != -1) return fail(BAP_EINVAL, "labels must be +1 or -1");
+        for (int q = 0; q < d; ++q)
+            if (!(X[(size_t)j * d + q] > 0)) return fail(BAP_EINVAL, "points must be positive");
+    }
+    AllocScope scope(o->stream);
+    cudaStream_t st = o->stream;
+    const int ms = p->boost == 1 ? 2 * p->n_stumps : p->n_stumps;
+    if (o->rule_kind != R_CMC || o->max_stumps != ms) TRY(set_rule_cmc(o, ms));
+    TRY(o->start.reserve((size_t)J * d * 8));
+    TRY(o->label.reserve((size_t)J * 4));
+    TRY(o->label_y.reserve((size_t)J * 8));
+    TRY(reserve_boost(o, J));
+    CU(cudaMemcpyAsync(o->start.p, X, (size_t)J * d * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(o->label.p, labels, (size_t)J * 4, cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(o->label_y.p, 0, (size_t)J * 8, st));
+    BoostPlan bp;
+    TRY(boost_plan(o, p, &bp));
+    TRY(enqueue_boost(o, bp, p, m));
+    const size_t base = (size_t)m * ms;
+    std::vector<int> f(ms), pl(ms);
+    std::vector<double> th(ms), al(ms);
+    int cnt = 0;
+    CU(cudaMemcpyAsync(&cnt, o->n_stumps.as<int>() + m, 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(f.data(), o->feat.as<int>() + base, ms * 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(pl.data(), o->pol.as<int>() + base, ms * 4, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(th.data(), o->thr.as<double>() + base, ms * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(al.data(), o->alpha.as<double>() + base, ms * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    *n_stumps = cnt;
+    for (int i = 0; i < ms; ++i) {
+        stumps[4 * i + 0] = f[i];
+        stumps[4 * i + 1] = th[i];
+        stumps[4 * i + 2] = pl[i];
+        stumps[4 * i + 3] = al[i];
+    }
+    return BAP_OK;
+}
+
 bap_status bap_debug_rng(uint64_t seed, int purpose, int m, uint32_t w1, uint32_t step, int d,
                          int64_t count, uint32_t* words, double* z) {
     clear_error();
@@ -1598,10 +1794,11 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
 // The scratch of the path kernel (per-unit partial sums, per-item unit counters, the work
 // counter, the item count and the step total) lives in one fixed array in this library's device
 // image instead of in buffers from cudaMalloc.  Every GPU that loads the library holds the array
-// until the process exits.  Host code never names the array as an address: the first call on a
-// device looks its address up with cudaGetSymbolAddress (with that device current) and caches
-// it.  All calls share the array and it keeps the last call's contents, so the call clears what
-// must start at zero; calls whose work overlaps on the GPU race on it.
+// until the process exits.  Host code never names the array as an address: every call looks its
+// address up with cudaGetSymbolAddress, with the option's device current (the first lookup on a
+// device loads the library's device image there if that has not happened yet).  All calls
+// share the array and it keeps the last call's contents, so the call clears what must start at
+// zero; calls whose work overlaps on the GPU race on it.
 
 #define BAP_STATIC_SCRATCH_BYTES (4u << 20)
 
@@ -1609,14 +1806,16 @@ static __device__ __align__(256) unsigned char bap_static_scratch[BAP_STATIC_SCR
 
 namespace {
 
-constexpr int kMaxStaticDevices = 64;
-std::mutex g_static_mu;
-unsigned char* g_static_base[kMaxStaticDevices] = {nullptr};
-
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 // Header of the array: [0] work counter (u64), [8] step total (u64), [16] item count (int).
-__global__ void static_scratch_clear_kernel(unsigned char* base, int n_items, size_t done_off) {
+// Besides clearing, this kernel checks the caller's inputs on the device: an item whose pivot is
+// outside -1..d-1 or whose start point has a coordinate that is not positive is marked bad, and
+// the path kernel gets a copy of the pivots with such pivots replaced by -1, so that no pivot
+// ever indexes outside the item's start point.
+__global__ void static_scratch_clear_kernel(unsigned char* base, int n_items, int d, size_t done_off,
+                                            size_t piv_off, size_t bad_off, const int* pivots,
+                                            const double* starts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *reinterpret_cast<unsigned long long*>(base) = 0ULL;
@@ -1624,7 +1823,32 @@ __global__ void static_scratch_clear_kernel(unsigned char* base, int n_items, si
         *reinterpret_cast<int*>(base + 16) = n_items;
     }
     int* done = reinterpret_cast<int*>(base + done_off);
-    for (int k = i; k < n_items; k += gridDim.x * blockDim.x) done[k] = 0;
+    int* piv = reinterpret_cast<int*>(base + piv_off);
+    int* bad = reinterpret_cast<int*>(base + bad_off);
+    for (int k = i; k < n_items; k += gridDim.x * blockDim.x) {
+        done[k] = 0;
+        int b = 0;
+        int p = pivots ? pivots[k] : -1;
+        if (p < -1 || p >= d) { b = 1; p = -1; }
+        for (int q = 0; q < d; ++q)
+            if (!(starts[(size_t)k * d + q] > 0.0)) b = 1;   // also catches NaN
+        piv[k] = p;
+        bad[k] = b;
+    }
+}
+
+// Items marked bad get NaN sums and -1 steps (their paths ran on the clamped pivot; no access
+// left the caller's buffers).
+__global__ void static_mark_bad_kernel(const int* bad, int n_items, double* sums, long long* steps) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_items; k += gridDim.x * blockDim.x) {
+        if (bad[k]) {
+            const double nan = __longlong_as_double(0x7ff8000000000000LL);
+            sums[3 * (size_t)k + 0] = nan;
+            sums[3 * (size_t)k + 1] = nan;
+            sums[3 * (size_t)k + 2] = nan;
+            steps[k] = -1;
+        }
+    }
 }
 
 }  // namespace
@@ -1642,7 +1866,9 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     const long long C = (N + chunk - 1) / chunk;
     const long long units = (long long)n_items * C;
     const size_t done_off = 256;
-    const size_t steps_off = done_off + align256((size_t)n_items * 4);
+    const size_t piv_off = done_off + align256((size_t)n_items * 4);
+    const size_t bad_off = piv_off + align256((size_t)n_items * 4);
+    const size_t steps_off = bad_off + align256((size_t)n_items * 4);
     const size_t partial_off = steps_off + align256((size_t)units * 8);
     const size_t need = partial_off + (size_t)units * 24;
     if (need > BAP_STATIC_SCRATCH_BYTES)
@@ -1653,20 +1879,20 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     int dev = -1;
     CU(cudaGetDevice(&dev));
     if (dev != o->device) return fail(BAP_EINVAL, "the option's device %d is not current (%d)", o->device, dev);
-    if (dev < 0 || dev >= kMaxStaticDevices) return fail(BAP_EINVAL, "device %d out of range", dev);
-    unsigned char* base;
+    // The array's device address, looked up on every call (cheap next to the kernels): after a
+    // device reset the image may be loaded at another address.
+    unsigned char* base = nullptr;
     {
-        std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_base[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, bap_static_scratch);
-            if (e != cudaSuccess || !p)
-                return fail(BAP_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
-            g_static_base[dev] = static_cast<unsigned char*>(p);
-        }
-        base = g_static_base[dev];
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, bap_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(BAP_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+        base = static_cast<unsigned char*>(p);
     }
-    static_scratch_clear_kernel<<<std::min(1024, (n_items + 255) / 256), 256, 0, o->stream>>>(base, n_items, done_off);
+    const int clear_blocks = std::max(1, std::min(1024, (n_items + 255) / 256));
+    static_scratch_clear_kernel<<<clear_blocks, 256, 0, o->stream>>>(
+        base, n_items, o->d, done_off, piv_off, bad_off, d_pivots, d_starts);
+    ++o->launches;
     CU(cudaGetLastError());
 
     PathArgs a;
@@ -1681,23 +1907,16 @@ extern "C" bap_status bap_continuation_static(bap_option* o, int m, int purpose,
     a.total_steps = reinterpret_cast<unsigned long long*>(base + 8);
     a.start = const_cast<double*>(d_starts);
     a.ctr_item = d_item_ids;
-    a.pivot = d_pivots;
+    a.pivot = d_pivots ? reinterpret_cast<const int*>(base + piv_off) : nullptr;
     a.done = reinterpret_cast<int*>(base + done_off);
     a.partial_steps = reinterpret_cast<long long*>(base + steps_off);
     a.partial = reinterpret_cast<double*>(base + partial_off);
     a.out_sums = d_sums;
     a.out_steps = reinterpret_cast<long long*>(d_steps);
-
-    const int rule = kernel_rule(o, o->rule_kind);
-    const void* fn = path_fn(o->d, rule, false);
-    if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
-    const size_t smem = path_smem_bytes(a, rule, false, o->d);
-    if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
-    int bps = 1;
-    TRY(path_blocks_per_sm(fn, o->device, smem, &bps));
-    long long blocks = (units + (kBlock / 32) - 1) / (kBlock / 32);
-    blocks = std::max(1LL, std::min(blocks, (long long)o->sm_count * bps));
-    void* args[] = {&a};
-    CU(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, smem, o->stream));
+    TRY(launch_path(o, a, o->rule_kind, false, units, /*no_events=*/true));
+    static_mark_bad_kernel<<<clear_blocks, 256, 0, o->stream>>>(
+        reinterpret_cast<const int*>(base + bad_off), n_items, d_sums, reinterpret_cast<long long*>(d_steps));
+    ++o->launches;
+    CU(cudaGetLastError());
     return BAP_OK;
 }

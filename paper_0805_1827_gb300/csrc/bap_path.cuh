@@ -9,7 +9,8 @@
 // unit belongs to one warp, taken from a device counter (persistent grid).  Inside a warp every
 // lane runs one path at a time and takes the next path index of the chunk as soon as its path
 // stops (warp ballot), so early-stopped paths leave no idle lanes.  Results per unit are summed
-// per lane (FP32, flushed to FP64 every 16 paths), reduced across the warp in a fixed shuffle
+// per lane (FP32, flushed to FP64 after every block of at most 32 warp steps), reduced across
+// the warp in a fixed shuffle
 // tree and written to a fixed slot; the warp that completes an item's last unit sums the slots
 // in fixed order, so results are bitwise reproducible whatever the scheduling.  That warp then
 // runs the item's epilogue on the device: the Newton update of an I&Z boundary point (and its
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                 if (a.mode == MODE_SUMS || a.mode == MODE_TRACE) {
                     // the pathwise derivative is with respect to the pivot's start value x
                     const int pv = a.pivot ? a.pivot[item] : -1;
-                    const double xs = pv >= 0 ? a.start[(size_t)item * D + pv] : 1.0;
+                    const double xs = (pv >= 0 && pv < D) ? a.start[(size_t)item * D + pv] : 1.0;
                     a.out_sums[3 * item + 0] = t0;
                     a.out_sums[3 * item + 1] = t1;
                     a.out_sums[3 * item + 2] = t2 / xs;

@@ -75,3 +75,40 @@ def test_static_scratch_rejects_calls_beyond_its_size():
     assert st == bap.BAP_EINVAL
     assert b"static scratch" in bap.lib().bap_last_error()
     opt.close()
+
+
+def test_static_scratch_marks_bad_inputs_without_touching_other_items():
+    """The call cannot see device data on the host, so it checks the inputs on the device: an
+    item whose pivot is outside -1..d-1 or whose start point has a coordinate <= 0 comes back
+    with NaN sums and steps = -1, and every other item is computed as usual."""
+    torch = pytest.importorskip("torch")
+    spec = spec_max_call(3, 100.0, rho=0.2, n_dates=5, T=1.0)
+    opt = bap.Option(spec)
+    n, N, m, seed = 6, 3000, 2, 4
+    starts = np.full((n, spec.d), 100.0)
+    starts[:, 0] = [90.0, 110.0, 120.0, 95.0, 105.0, 130.0]
+    ids = np.arange(n, dtype=np.int32)
+    piv = np.zeros(n, dtype=np.int32)
+    ref_sums, ref_steps = opt.debug_continuation(m, PURPOSE_IZ, seed, ids, starts, N, piv)
+    bad_piv, bad_start = 1, 4
+    piv_in = piv.copy()
+    piv_in[bad_piv] = spec.d                 # one past the last asset
+    starts_in = starts.copy()
+    starts_in[bad_start, 2] = 0.0
+    d_ids = torch.tensor(ids, dtype=torch.int32, device="cuda")
+    d_piv = torch.tensor(piv_in, dtype=torch.int32, device="cuda")
+    d_starts = torch.tensor(starts_in, dtype=torch.float64, device="cuda")
+    d_sums = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    d_steps = torch.zeros(n, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    st = _fn()(opt.h, m, PURPOSE_IZ, seed, n, d_ids.data_ptr(), d_piv.data_ptr(),
+               d_starts.data_ptr(), N, d_sums.data_ptr(), d_steps.data_ptr())
+    assert st == bap.BAP_OK, bap.lib().bap_last_error()
+    torch.cuda.synchronize()
+    got, steps = d_sums.cpu().numpy(), d_steps.cpu().numpy()
+    bad = np.zeros(n, dtype=bool)
+    bad[[bad_piv, bad_start]] = True
+    assert np.all(np.isnan(got[bad])) and np.all(steps[bad] == -1)
+    assert np.allclose(got[~bad], ref_sums[~bad], rtol=1e-12, atol=0.0)
+    assert np.array_equal(steps[~bad], ref_steps[~bad])
+    opt.close()
