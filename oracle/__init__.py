@@ -413,24 +413,15 @@ def basis_matrix(Y: np.ndarray, degree: int) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
-def rank_deficient(A: np.ndarray, tol: float = 1e-13) -> bool:
-    """The design's Gram matrix, scaled to a unit diagonal, meets a Cholesky pivot <= tol: its
-    columns are numerically dependent (e.g. a small Korobov point set)."""
-    G = A.T @ A
-    dg = np.diag(G)
-    if np.any(dg <= 0):
+def rank_deficient(A: np.ndarray) -> bool:
+    """The design has numerical rank below its column count: the singular values of the design
+    with its columns scaled to unit length, against numpy's standard rank tolerance
+    (sigma_max x max(rows, columns) x machine epsilon).  Small Korobov point sets are, e.g. 48
+    points in 4 variables span 31 of the 35 cubic monomials."""
+    nrm = np.linalg.norm(A, axis=0)
+    if np.any(nrm <= 0):
         return True
-    s = 1.0 / np.sqrt(dg)
-    G = G * np.outer(s, s)
-    p = G.shape[0]
-    L = np.zeros_like(G)
-    for j in range(p):
-        v = G[j, j] - L[j, :j] @ L[j, :j]
-        if not v > tol:
-            return True
-        L[j, j] = np.sqrt(v)
-        L[j + 1:, j] = (G[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
-    return False
+    return int(np.linalg.matrix_rank(A / nrm)) < A.shape[1]
 
 
 def ls_fit(Y: np.ndarray, x: np.ndarray, K: float, degree: int, use=None) -> np.ndarray:
@@ -562,53 +553,67 @@ def stump_predict(Fx: np.ndarray, feat: int, thr: float, pol: int) -> np.ndarray
     return np.where(Fx[:, feat] > thr, pol, -pol)
 
 
+AB_TIE = 1e-12         # stumps whose weighted errors are within this of the least tie
+
+
+def adaboost_candidates(Fx: np.ndarray, labels: np.ndarray, w: np.ndarray):
+    """Every decision stump of one AdaBoost round with its weighted error, in the tie-break order
+    (feature, threshold ascending, polarity +1 then -1), as arrays (error, feature, threshold,
+    polarity).  Per feature: a threshold below every value (a constant vote) and the midpoints
+    between consecutive distinct sorted values; polarity +1 votes +1 above the threshold.  Error
+    of polarity +1 at a threshold = weight of the positives below it + weight of the negatives
+    above it (FP64 prefix sums in sorted order); polarity -1 errs on the rest."""
+    J, nf = Fx.shape
+    y = labels.astype(np.float64)
+    W = w.sum()
+    errs, feats, thrs, pols = [], [], [], []
+    for f in range(nf):
+        o = np.argsort(Fx[:, f], kind="stable")
+        v, yy, ww = Fx[o, f], y[o], w[o]
+        wpos = np.cumsum(np.where(yy > 0, ww, 0.0))
+        wneg = np.cumsum(np.where(yy < 0, ww, 0.0))
+        neg_tot = wneg[-1]
+        valid = v[1:] > v[:-1]
+        thr = (0.5 * (v[:-1] + v[1:]))[valid]
+        e_plus = (wpos[:-1] + (neg_tot - wneg[:-1]))[valid]
+        errs.append(np.concatenate([[neg_tot, W - neg_tot],
+                                    np.stack([e_plus, W - e_plus], axis=1).ravel()]))
+        thrs.append(np.concatenate([[-math.inf, -math.inf], np.repeat(thr, 2)]))
+        pols.append(np.concatenate([[1, -1], np.tile([1, -1], len(thr))]))
+        feats.append(np.full(2 + 2 * len(thr), f))
+    return (np.concatenate(errs), np.concatenate(feats), np.concatenate(thrs),
+            np.concatenate(pols))
+
+
+def adaboost_choice(cands):
+    """The round's stump: with e_min the least error, the first candidate whose error is at
+    most e_min + 1e-12.  Returns (error, feature, threshold, polarity)."""
+    errs, feats, thrs, pols = cands
+    i = int(np.flatnonzero(errs <= errs.min() + AB_TIE)[0])
+    return float(errs[i]), int(feats[i]), float(thrs[i]), int(pols[i])
+
+
 def adaboost(Fx: np.ndarray, labels: np.ndarray, n_stumps: int):
-    """Discrete AdaBoost with decision stumps (Section 3.2 names AdaBoost).  Candidate stumps per
-    feature: a threshold below every value (a constant vote) and the midpoints between
-    consecutive distinct sorted values; polarity +1 votes +1 above the threshold.  The stump of
-    least weighted error wins: with e_min the least error, the first candidate in (feature,
-    threshold ascending, polarity +1 then -1) order whose error is <= e_min + 1e-12.
-    alpha = 1/2 ln((1-eps)/eps), eps clamped to [1e-10, 1-1e-10]; stop before a stump with
-    eps >= 1/2 and after a perfect one."""
+    """Discrete AdaBoost with decision stumps (Section 3.2 names AdaBoost), plain FP64.  Uniform
+    initial weights; each round the stump of least weighted error (adaboost_candidates,
+    adaboost_choice); alpha = 1/2 ln((1-eps)/eps), eps = error / total weight clamped to
+    [1e-10, 1-1e-10]; weights times e^{-alpha y h}, then divided by their sum.  Stop before a
+    stump with eps >= 1/2 and after a perfect one.  Returns (feature, threshold, polarity,
+    alpha) per stump."""
     J, nf = Fx.shape
     y = labels.astype(np.float64)
     w = np.full(J, 1.0 / J)
     out = []
-    orders = [np.argsort(Fx[:, f], kind="stable") for f in range(nf)]
     for _ in range(n_stumps):
         W = w.sum()
-        errs, thrs, pols, feats = [], [], [], []
-        for f in range(nf):
-            o = orders[f]
-            v, yy, ww = Fx[o, f], y[o], w[o]
-            wpos = np.cumsum(np.where(yy > 0, ww, 0.0))
-            wneg = np.cumsum(np.where(yy < 0, ww, 0.0))
-            neg_tot = wneg[-1]
-            # Error of polarity +1 at the threshold between sorted positions i and i+1:
-            # positives on the left (voted -1) plus negatives on the right (voted +1).
-            valid = v[1:] > v[:-1]
-            thr = (0.5 * (v[:-1] + v[1:]))[valid]
-            e_plus = (wpos[:-1] + (neg_tot - wneg[:-1]))[valid]
-            e = np.concatenate([[neg_tot, W - neg_tot],
-                                np.stack([e_plus, W - e_plus], axis=1).ravel()])
-            t = np.concatenate([[-math.inf, -math.inf], np.repeat(thr, 2)])
-            p = np.concatenate([[1, -1], np.tile([1, -1], len(thr))])
-            errs.append(e)
-            thrs.append(t)
-            pols.append(p)
-            feats.append(np.full(len(e), f))
-        errs, thrs = np.concatenate(errs), np.concatenate(thrs)
-        pols, feats = np.concatenate(pols), np.concatenate(feats)
-        e_min = errs.min()
-        i = int(np.flatnonzero(errs <= e_min + 1e-12)[0])
-        e, f, thr, pol = errs[i], int(feats[i]), float(thrs[i]), int(pols[i])
+        e, f, thr, pol = adaboost_choice(adaboost_candidates(Fx, labels, w))
         eps = e / W
         if eps >= 0.5 - 1e-12:
             break
         eps_c = min(max(eps, 1e-10), 1.0 - 1e-10)
         alpha = 0.5 * math.log((1.0 - eps_c) / eps_c)
         h = stump_predict(Fx, f, thr, pol)
-        out.append((f, thr, pol, alpha))
+        out.append((int(f), float(thr), int(pol), alpha))
         w = w * np.exp(-alpha * y * h)
         w = w / w.sum()
         if eps <= 1e-10:
@@ -616,51 +621,83 @@ def adaboost(Fx: np.ndarray, labels: np.ndarray, n_stumps: int):
     return out
 
 
-LB_FIX = 2.0 ** 48     # fixed-point scale of LogitBoost's weighted sums
+def adaboost_weights(Fx: np.ndarray, labels: np.ndarray, stumps):
+    """The AdaBoost weights after the given stumps (the textbook update of adaboost), starting
+    from uniform weights."""
+    y = labels.astype(np.float64)
+    w = np.full(len(y), 1.0 / len(y))
+    for f, thr, pol, alpha in stumps:
+        w = w * np.exp(-alpha * y * stump_predict(Fx, f, thr, pol))
+        w = w / w.sum()
+    return w
+
+
 LB_ZMAX = 4.0          # working responses are clamped to [-LB_ZMAX, LB_ZMAX]
+LB_TIE = 1e-12         # candidates within this relative distance of the largest gain tie
+
+
+def logit_working(F: np.ndarray, labels: np.ndarray):
+    """One LogitBoost round's working weights and responses (Friedman, Hastie and Tibshirani):
+    p = 1 / (1 + e^{-2F}), w = p (1 - p), z = (y* - p) / w clamped to [-4, 4], y* = 1 for label
+    +1, else 0.  A point whose w is exactly 0 (p rounded to 0 or 1) carries no weight; its z is
+    set to 0."""
+    ys = (labels > 0).astype(np.float64)
+    with np.errstate(over="ignore"):
+        p = 1.0 / (1.0 + np.exp(-2.0 * F))
+    w = p * (1.0 - p)
+    z = np.zeros_like(w)
+    pos = w > 0
+    z[pos] = np.clip((ys[pos] - p[pos]) / w[pos], -LB_ZMAX, LB_ZMAX)
+    return w, z
+
+
+def logit_candidates(Fx: np.ndarray, w: np.ndarray, z: np.ndarray):
+    """Every regression stump of one round with its weighted least-squares gain, in the
+    tie-break order (no split first, then feature, threshold ascending): tuples (gain, feature,
+    threshold, c_L, c_R).  A split between consecutive distinct sorted values of a feature has
+    gain S_L^2 / W_L + S_R^2 / W_R (W = sum of w, S = sum of w z over each side, FP64 sums in
+    sorted order); no split gains S^2 / W.  Splits with an empty-weight side are skipped."""
+    J, nf = Fx.shape
+    wz = w * z
+    W, S = float(w.sum()), float(wz.sum())
+    if not W > 0:
+        return []
+    cands = [(S * S / W, 0, -math.inf, S / W, S / W)]
+    for f in range(nf):
+        o = np.argsort(Fx[:, f], kind="stable")
+        v = Fx[o, f]
+        WL, SL = np.cumsum(w[o])[:-1], np.cumsum(wz[o])[:-1]
+        WR, SR = W - WL, S - SL
+        ok = (v[1:] > v[:-1]) & (WL > 0) & (WR > 0)
+        for i in np.flatnonzero(ok):
+            g = SL[i] * SL[i] / WL[i] + SR[i] * SR[i] / WR[i]
+            cands.append((float(g), f, 0.5 * (v[i] + v[i + 1]), SL[i] / WL[i], SR[i] / WR[i]))
+    return cands
+
+
+def logit_choice(cands):
+    """The round's stump: with G the largest gain, the first candidate whose gain is at least
+    G (1 - 1e-12)."""
+    G = max(c[0] for c in cands)
+    return next(c for c in cands if c[0] >= G * (1.0 - LB_TIE))
 
 
 def logitboost(Fx: np.ndarray, labels: np.ndarray, n_rounds: int):
     """Two-class LogitBoost with regression stumps (Section 3.2 names LogitBoost beside
-    AdaBoost; the algorithm of Friedman, Hastie and Tibshirani, Ann. Statist. 28 (2000)):
-    F = 0; each round p = 1 / (1 + e^{-2F}), w = p (1 - p), z = (y* - p) / w clamped to
-    [-4, 4] (y* = 1 for label +1, else 0), then the weighted least-squares regression stump
-    f(x) = c_L for x_f <= t, c_R above, and F <- F + f / 2.
-
-    The stump search sums w and w z in order of each feature in fixed point (round(v 2^48),
-    exact), so the choice does not depend on summation order: a split after sorted position
-    i between distinct values gains S_L^2 / W_L + S_R^2 / W_R (FP64 from the exact sums;
-    no split gains S^2 / W); with G the largest gain the first candidate in (no split, then
-    feature, threshold ascending) order with gain >= G (1 - 1e-12) wins; c = S / W per side.
-    Returns the rounds as (feature, threshold, c_L, c_R), threshold -inf for no split."""
+    AdaBoost; the algorithm of Friedman, Hastie and Tibshirani, Ann. Statist. 28 (2000)), plain
+    FP64: F = 0; each round the working weights and responses (logit_working), the weighted
+    least-squares regression stump f(x) = c_L for x_f <= t, c_R above (logit_candidates,
+    logit_choice; c = S / W per side), and F <- F + f / 2.  Returns the rounds as (feature,
+    threshold, c_L, c_R), threshold -inf for no split."""
     J, nf = Fx.shape
-    ys = (labels > 0).astype(np.float64)
     F = np.zeros(J)
-    orders = [np.argsort(Fx[:, f], kind="stable") for f in range(nf)]
     out = []
     for _ in range(n_rounds):
-        p = 1.0 / (1.0 + np.exp(-2.0 * F))
-        w = p * (1.0 - p)
-        z = np.clip((ys - p) / w, -LB_ZMAX, LB_ZMAX)
-        wq = np.rint(w * LB_FIX).astype(np.int64)
-        sq = np.rint(w * z * LB_FIX).astype(np.int64)
-        W, S = int(wq.sum()), int(sq.sum())
-        if W <= 0:
+        w, z = logit_working(F, labels)
+        cands = logit_candidates(Fx, w, z)
+        if not cands:
             break
-        cands = [(float(S) * float(S) / float(W), 0, -math.inf, float(S) / float(W),
-                  float(S) / float(W))]
-        for f in range(nf):
-            o = orders[f]
-            v = Fx[o, f]
-            cw, cs = np.cumsum(wq[o])[:-1], np.cumsum(sq[o])[:-1]    # left of each split
-            WL, SL = cw.astype(np.float64), cs.astype(np.float64)
-            WR, SR = (W - cw).astype(np.float64), (S - cs).astype(np.float64)
-            ok = (v[1:] > v[:-1]) & (cw > 0) & (W - cw > 0)
-            for i in np.flatnonzero(ok):
-                g = SL[i] * SL[i] / WL[i] + SR[i] * SR[i] / WR[i]
-                cands.append((g, f, 0.5 * (v[i] + v[i + 1]), SL[i] / WL[i], SR[i] / WR[i]))
-        G = max(c[0] for c in cands)
-        _, f, thr, cl, cr = next(c for c in cands if c[0] >= G * (1.0 - 1e-12))
+        _, f, thr, cl, cr = logit_choice(cands)
         F = F + 0.5 * np.where(Fx[:, f] > thr, cr, cl)
         out.append((int(f), float(thr), float(cl), float(cr)))
     return out

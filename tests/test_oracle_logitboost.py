@@ -8,7 +8,8 @@ import oracle
 
 def test_first_round_by_hand():
     """x = 1..4 with labels -,-,+,+: F = 0 so p = 1/2, w = 1/4, z = +-2.  The split after x = 2
-    gains (2^48)^2 / 2^47 twice = 2^50, the most; c_L = -2, c_R = +2; F becomes -+1.  Written as
+    has W_L = W_R = 1/2 and S_L = -1, S_R = +1, so it gains 1/(1/2) + 1/(1/2) = 4, the most (no
+    split gains 0, the other splits 8/3 and 8/3); c_L = -2, c_R = +2; F becomes -+1.  Written as
     vote stumps: B = (2 - (-2)) / 4 = 1 at 2.5, A = 0."""
     Fx = np.array([[1.0], [2.0], [3.0], [4.0]])
     lab = np.array([-1, -1, 1, 1])
@@ -105,3 +106,26 @@ def test_fp32_split_gain_is_within_the_prefilter_bound():
         if exact > 0:
             worst = max(worst, abs(g32 - exact) / exact)
     assert worst < 4e-7, worst
+
+
+def test_gains_of_the_first_round_by_hand():
+    """The candidate gains of the same first round, written out: no split 0, after x = 1:
+    (-1/2)^2/(1/4) + (1/2)^2/(3/4) = 4/3, after x = 2: 4, after x = 3: 4/3."""
+    Fx = np.array([[1.0], [2.0], [3.0], [4.0]])
+    lab = np.array([-1, -1, 1, 1])
+    w, z = oracle.logit_working(np.zeros(4), lab)
+    assert np.allclose(w, 0.25) and np.allclose(z, [-2, -2, 2, 2])
+    g = [(c[0], c[2]) for c in oracle.logit_candidates(Fx, w, z)]
+    assert g[0][0] == 0.0 and math.isinf(g[0][1])
+    assert [t for _, t in g[1:]] == [1.5, 2.5, 3.5]
+    assert np.allclose([v for v, _ in g[1:]], [4.0 / 3.0, 4.0, 4.0 / 3.0], rtol=1e-15)
+
+
+def test_saturated_points_carry_no_weight():
+    """Once |F| is so large that p rounds to 0 or 1, w = p (1 - p) is 0 and the point drops out
+    of every sum (its response is set to 0 rather than 0/0)."""
+    F = np.array([0.0, 40.0, -400.0, 0.3])   # p = 1 and p = 0 exactly
+    lab = np.array([1, 1, -1, -1])
+    w, z = oracle.logit_working(F, lab)
+    assert w[1] == 0.0 and w[2] == 0.0 and z[1] == 0.0 and z[2] == 0.0
+    assert np.all(np.isfinite(w * z))
