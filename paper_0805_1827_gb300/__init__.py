@@ -33,7 +33,8 @@ EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch
             "bap_debug_checks", "bap_checked_build",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
-            "bap_debug_rng", "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
+            "bap_debug_rng", "bap_debug_newton", "bap_debug_ls_fit", "bap_debug_boost",
+            "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
             "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait", "bap_cancel",
             "bap_server_get_stats", "bap_server_destroy"]
 LAUNCH_PLAIN, LAUNCH_GRAPH, LAUNCH_COOP = 0, 1, 2
@@ -139,6 +140,10 @@ def lib():
                                       ip, dp]
         L.bap_debug_rng.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_int,
                                     C.c_int64, C.POINTER(C.c_uint32), dp]
+        L.bap_debug_newton.argtypes = [vp, C.POINTER(_IZ), C.c_int, C.c_int, ip, ip, dp, dp, ip,
+                                       ip, dp, dp, i64p]
+        L.bap_debug_ls_fit.argtypes = [vp, C.c_int, C.c_int, dp, dp, ip, dp]
+        L.bap_debug_boost.argtypes = [vp, C.POINTER(_CMC), C.c_int, dp, ip, ip, dp]
         L.bap_destroy.argtypes = [vp]
         L.bap_destroy.restype = None
         L.bap_last_error.restype = C.c_char_p
@@ -283,6 +288,57 @@ class Option:
                                             None if piv is None else _ip(piv), _dp(starts), N,
                                             _dp(sums), steps.ctypes.data_as(C.POINTER(C.c_int64))))
         return sums, steps
+
+    def debug_newton(self, params, m: int, item_ids, pivots, starts, bracket: bool = False):
+        """Newton boundary points of date m for the given items under the option's current
+        rules: (x, evaluations, status, inner path-steps), plus the final brackets (lo, hi) with
+        bracket=True."""
+        starts = _f64(np.atleast_2d(starts))
+        n = starts.shape[0]
+        ids = np.ascontiguousarray(item_ids, dtype=np.int32)
+        piv = np.ascontiguousarray(pivots, dtype=np.int32)
+        c = _IZ(params.J, params.N1, params.f_tol, params.x_tol, params.max_iter, params.degree,
+                params.seed, params.fixed_point, params.fp_eps, getattr(params, "warm_start", 0))
+        x = np.zeros(n)
+        it = np.zeros(n, dtype=np.int32)
+        st = np.zeros(n, dtype=np.int32)
+        steps = np.zeros(1, dtype=np.int64)
+        lo, hi = np.zeros(n), np.zeros(n)
+        _check(lib().bap_debug_newton(self.h, C.byref(c), m, n, _ip(ids), _ip(piv), _dp(starts),
+                                      _dp(x), _ip(it), _ip(st), _dp(lo), _dp(hi),
+                                      steps.ctypes.data_as(C.POINTER(C.c_int64))))
+        if bracket:
+            return x, it, st, int(steps[0]), lo, hi
+        return x, it, st, int(steps[0])
+
+    def debug_ls_fit(self, degree: int, J: int, starts, x, status) -> np.ndarray:
+        """Device least-squares boundary of one date: (n_bnd, n_coef) coefficients."""
+        d = self.spec.d
+        s = d - 1
+        if s == 0:
+            degree = 0
+        n_bnd = d if self.spec.payoff == "max_call" and d > 1 else 1
+        p = 1 + (s if degree >= 1 else 0) + (s * (s + 1) // 2 if degree >= 2 else 0) + \
+            (s * (s + 1) * (s + 2) // 6 if degree >= 3 else 0)
+        starts = _f64(np.atleast_2d(starts))
+        x = _f64(x)
+        st = np.ascontiguousarray(status, dtype=np.int32)
+        coef = np.zeros((n_bnd, p))
+        _check(lib().bap_debug_ls_fit(self.h, degree, J, _dp(starts), _dp(x), _ip(st), _dp(coef)))
+        return coef
+
+    def debug_boost(self, params, m: int, X, labels):
+        """Device boosting of date m on the given points and labels: the stumps as a list of
+        (feature, threshold, polarity, alpha)."""
+        X = _f64(np.atleast_2d(X))
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        c = _CMC(params.J, params.N2, params.n_stumps, params.seed, getattr(params, "sampler", 0),
+                 getattr(params, "boost", 0))
+        ms = params.n_stumps * (2 if getattr(params, "boost", 0) == 1 else 1)
+        out = np.zeros((ms, 4))
+        n = C.c_int(0)
+        _check(lib().bap_debug_boost(self.h, C.byref(c), m, _dp(X), _ip(lab), C.byref(n), _dp(out)))
+        return [(int(f), float(t), int(pl), float(a)) for f, t, pl, a in out[:n.value]]
 
     def debug_paths(self, m: int, purpose: int, seed: int, item_id: int, start, N: int):
         start = _f64(start)

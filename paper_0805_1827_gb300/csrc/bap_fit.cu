@@ -83,30 +83,16 @@ __global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_
 // I&Z items of date m (item = b*J + j): the other assets at the lognormal quantiles of the
 // shifted lattice point frac(j g / J + 1/(2J)), the pivot at the Newton start, and the bracket.
 
-__global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
-                                double* start, ItemState* state, int* pivot, int* active,
-                                int* count, const double* coef64, int n_coef, int degree,
-                                const int* fitted, int warm_start) {
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= n_bnd * J) return;
+// Newton state of one boundary point whose other coordinates S[q], q != p, are set: the initial
+// bracket and iterate (Section 2.3: Newton's iterations from an approximate point), warm-started
+// at the later date's fitted boundary when asked; writes the initial iterate to S[p] and returns
+// whether the point needs evaluations (false: no root, e.g. a put whose other assets alone
+// exceed the strike).  b = the boundary whose later-date coefficients seed a warm start.
+__device__ bool newton_item_init(const DevModel* M, int m, int n_bnd, int b, int p, double* S,
+                                 ItemState& st, const double* coef64, int n_coef, int degree,
+                                 const int* fitted, int warm_start) {
     const int d = M->d, s = d - 1;
-    const int b = item / J, j = item - b * J;
-    const int p = n_bnd > 1 ? b : 0;
-    const double tm = M->t[m];
     const double K = M->K;
-    double* S = start + (size_t)item * d;
-    unsigned long long g = 1;
-    const unsigned long long a = (unsigned long long)(*korobov_a);
-    int c = 0;
-    for (int q = 0; q < d; ++q) {
-        if (q == p) continue;
-        const double u = ((double)(((unsigned long long)j * g) % (unsigned long long)J) + 0.5) / (double)J;
-        const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
-        S[q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * normcdfinv(u));
-        g = (g * a) % (unsigned long long)J;
-        ++c;
-    }
-    ItemState st;
     st.iters = 0;
     st.status = ST_OK;
     st.done = 0;
@@ -170,12 +156,72 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
         if (xw > st.lo && xw < st.hi) st.x = xw;
     }
     S[p] = st.x;
+    return live;
+}
+
+__global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
+                                double* start, ItemState* state, int* pivot, int* active,
+                                int* count, const double* coef64, int n_coef, int degree,
+                                const int* fitted, int warm_start) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= n_bnd * J) return;
+    const int d = M->d;
+    const int b = item / J, j = item - b * J;
+    const int p = n_bnd > 1 ? b : 0;
+    const double tm = M->t[m];
+    double* S = start + (size_t)item * d;
+    unsigned long long g = 1;
+    const unsigned long long a = (unsigned long long)(*korobov_a);
+    for (int q = 0; q < d; ++q) {
+        if (q == p) continue;
+        const double u = ((double)(((unsigned long long)j * g) % (unsigned long long)J) + 0.5) / (double)J;
+        const double mu = M->r - M->delta[q] - 0.5 * M->sigma[q] * M->sigma[q];
+        S[q] = M->S0[q] * exp(mu * tm + M->sigma[q] * sqrt(tm) * normcdfinv(u));
+        g = (g * a) % (unsigned long long)J;
+    }
+    ItemState st;
+    const bool live = newton_item_init(M, m, n_bnd, b, p, S, st, coef64, n_coef, degree, fitted,
+                                       warm_start);
     state[item] = st;
     pivot[item] = p;
     if (live) {
         const int pos = atomicAdd(count, 1);
         active[pos] = item;
     }
+}
+
+// The same set-up for caller-given points (the parity hook bap_debug_newton): item i starts from
+// starts_in[i] (its pivot coordinate is replaced by the initial iterate), with pivot pivots_in[i]
+// and counter word ctr_in[i].  Items enter the first pass's list in index order, so the pass's
+// work split does not depend on thread scheduling.
+__global__ void newton_items_setup_kernel(const DevModel* M, int m, int n_items, int n_bnd,
+                                          const double* starts_in, const int* pivots_in,
+                                          const int* ctr_in, double* start, ItemState* state,
+                                          int* pivot, int* ctr_item, int* live_flag,
+                                          const double* coef64, int n_coef, int degree,
+                                          const int* fitted, int warm_start) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= n_items) return;
+    const int d = M->d;
+    const int p = pivots_in[item];
+    double* S = start + (size_t)item * d;
+    for (int q = 0; q < d; ++q) S[q] = starts_in[(size_t)item * d + q];
+    ItemState st;
+    const bool live = newton_item_init(M, m, n_bnd, n_bnd > 1 ? p : 0, p, S, st, coef64, n_coef,
+                                       degree, fitted, warm_start);
+    state[item] = st;
+    pivot[item] = p;
+    ctr_item[item] = ctr_in[item];
+    live_flag[item] = live ? 1 : 0;
+}
+
+// Compacts the live items into the first pass's list in index order (one block).
+__global__ void newton_items_list_kernel(const int* live_flag, int n_items, int* active, int* count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 0;
+    for (int i = 0; i < n_items; ++i)
+        if (live_flag[i]) active[c++] = i;
+    *count = c;
 }
 
 // ---------------------------------------------------------------------------------------------

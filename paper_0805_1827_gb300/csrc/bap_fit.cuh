@@ -11,6 +11,13 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
                                 double* start, ItemState* state, int* pivot, int* active,
                                 int* count, const double* coef64, int n_coef, int degree,
                                 const int* fitted, int warm_start);
+__global__ void newton_items_setup_kernel(const DevModel* M, int m, int n_items, int n_bnd,
+                                          const double* starts_in, const int* pivots_in,
+                                          const int* ctr_in, double* start, ItemState* state,
+                                          int* pivot, int* ctr_item, int* live_flag,
+                                          const double* coef64, int n_coef, int degree,
+                                          const int* fitted, int warm_start);
+__global__ void newton_items_list_kernel(const int* live_flag, int n_items, int* active, int* count);
 __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
                                 int degree, double K, float* coef_f, double* coef_d);
 // Threads per block of ls_fit_kernel (one block per boundary).
