@@ -490,6 +490,10 @@ def run_ours(args) -> None:
     opts = [bap.Option(spec_max_call(5, s0, rho=0.3), stream=stream.cuda_stream) for s0 in S0S]
     for o in opts:
         o.set_launch_mode(mode)
+        if args.paths_per_lane:
+            o.set_paths_per_lane(args.paths_per_lane)
+        if args.unit_paths:
+            o.set_unit_paths(args.unit_paths)
     params = IZParams(J=J, N1=N1, degree=2, seed=1000 * rank + 1)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -636,6 +640,10 @@ def main():
                     help="skip the side-by-side fit timings (I&Z launch forms, CMC boosting forms)")
     ap.add_argument("--no-paper-tables", dest="paper_tables", action="store_false",
                     help="skip the paper's Tables 1-4 workloads and the root-finding study")
+    ap.add_argument("--paths-per-lane", type=int, default=0,
+                    help="path slots per lane of the I&Z path kernels (0: the library's choice)")
+    ap.add_argument("--unit-paths", type=int, default=0,
+                    help="paths per warp unit of the fits (0: the library's choice)")
     ap.add_argument("--J", type=int, default=0, help="override J (testing only)")
     ap.add_argument("--N1", type=int, default=0, help="override N1 (testing only)")
     args = ap.parse_args()

@@ -204,6 +204,20 @@ bap_status bap_debug_checks(bap_option *opt, uint64_t *count, int *first_code);
 /* 1 in the checked build, 0 in the normal one. */
 int bap_checked_build(void);
 
+/* Paths per warp unit of the fits' path launches (I&Z Newton passes, CMC labels): 0 (default)
+ * chooses from the launch shape (about 16k units of 64..2048 paths); else a multiple of 32 up to
+ * 65536.  Longer units spread a unit's fixed set-up and reduction over more paths; shorter ones
+ * balance passes with few points.  The choice changes how FP32 partial sums are grouped, so
+ * results differ between settings by rounding only.  Errors: EINVAL. */
+bap_status bap_set_unit_paths(bap_option *opt, int paths);
+
+/* Path slots per lane of the FP32 kernels with a quadratic (or lower) I&Z boundary: 1 (default)
+ * or 2.  With 2, every lane advances two paths per step, interleaved, which gives the warp
+ * schedulers more independent work; the kernel runs fewer resident blocks.  The choice changes
+ * how FP32 partial sums are grouped, so results differ from the other setting by rounding only.
+ * Errors: EINVAL (null option, ppl outside 1..2). */
+bap_status bap_set_paths_per_lane(bap_option *opt, int ppl);
+
 /* How bap_fit_classifier runs the AdaBoost of each date ([class], Section 3.2; the paper's
  * sequential bottleneck).  3 (default): form 2 for J <= 2048, form 1 above.  2: one 512-thread
  * block with one warp per feature, the sorted orders and weights held in shared memory; used when

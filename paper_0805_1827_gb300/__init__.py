@@ -30,6 +30,7 @@ MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
 EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
             "bap_set_boost_form", "bap_last_boost_form", "bap_set_wait_limit",
+            "bap_set_paths_per_lane", "bap_set_unit_paths",
             "bap_debug_checks", "bap_checked_build",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
@@ -114,6 +115,8 @@ def lib():
         L.bap_set_profiling.argtypes = [vp, C.c_int]
         L.bap_set_launch_mode.argtypes = [vp, C.c_int]
         L.bap_set_boost_form.argtypes = [vp, C.c_int]
+        L.bap_set_paths_per_lane.argtypes = [vp, C.c_int]
+        L.bap_set_unit_paths.argtypes = [vp, C.c_int]
         L.bap_set_wait_limit.argtypes = [vp, C.c_uint64]
         L.bap_debug_checks.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]
         L.bap_checked_build.argtypes = []
@@ -233,6 +236,12 @@ class Option:
 
     def set_wait_limit(self, ns: int):
         _check(lib().bap_set_wait_limit(self.h, ns))
+
+    def set_unit_paths(self, paths: int):
+        _check(lib().bap_set_unit_paths(self.h, paths))
+
+    def set_paths_per_lane(self, ppl: int):
+        _check(lib().bap_set_paths_per_lane(self.h, ppl))
 
     def set_boost_form(self, form: int):
         _check(lib().bap_set_boost_form(self.h, form))

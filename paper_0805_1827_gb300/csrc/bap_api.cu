@@ -125,18 +125,18 @@ bap_status path_blocks_per_sm(const void* fn, int device, size_t smem, int* bps)
     return BAP_OK;
 }
 
-const void* path_fn(int D, int rule, bool fp64) {
+const void* path_fn(int D, int rule, bool fp64, int ppl = 1) {
     switch (D) {
-        case 1: return path_kernel_fn<1>(rule, fp64);
-        case 2: return path_kernel_fn<2>(rule, fp64);
-        case 3: return path_kernel_fn<3>(rule, fp64);
-        case 4: return path_kernel_fn<4>(rule, fp64);
-        case 5: return path_kernel_fn<5>(rule, fp64);
-        case 6: return path_kernel_fn<6>(rule, fp64);
-        case 7: return path_kernel_fn<7>(rule, fp64);
-        case 8: return path_kernel_fn<8>(rule, fp64);
-        case 9: return path_kernel_fn<9>(rule, fp64);
-        case 10: return path_kernel_fn<10>(rule, fp64);
+        case 1: return path_kernel_fn<1>(rule, fp64, ppl);
+        case 2: return path_kernel_fn<2>(rule, fp64, ppl);
+        case 3: return path_kernel_fn<3>(rule, fp64, ppl);
+        case 4: return path_kernel_fn<4>(rule, fp64, ppl);
+        case 5: return path_kernel_fn<5>(rule, fp64, ppl);
+        case 6: return path_kernel_fn<6>(rule, fp64, ppl);
+        case 7: return path_kernel_fn<7>(rule, fp64, ppl);
+        case 8: return path_kernel_fn<8>(rule, fp64, ppl);
+        case 9: return path_kernel_fn<9>(rule, fp64, ppl);
+        case 10: return path_kernel_fn<10>(rule, fp64, ppl);
         default: return nullptr;
     }
 }
@@ -147,12 +147,14 @@ bool has_device(int* dev) {
     return cudaGetDevice(dev) == cudaSuccess;
 }
 
-// Paths per warp unit: a function of the launch shape only (so results do not depend on what
-// else runs): about 16k units, 64..2048 paths each, a multiple of 32.
-int choose_chunk(long long n_items, long long N) {
+// Paths per warp unit: a function of the launch shape (and of the option's unit setting) only,
+// so that results do not depend on what else runs.  Automatic (unit_paths = 0): about 16k
+// units, 64..2048 paths each, a multiple of 32; else unit_paths (a multiple of 32).
+int choose_chunk(long long n_items, long long N, int unit_paths = 0) {
     long long target = (n_items * N + 16383) / 16384;
     long long c = ((target + 31) / 32) * 32;
     c = std::max(64LL, std::min(2048LL, c));
+    if (unit_paths > 0) c = unit_paths;
     long long nr = ((N + 31) / 32) * 32;
     c = std::min(c, std::max(32LL, nr));
     // very long pricing runs: keep the unit count below 2^24
@@ -180,7 +182,7 @@ int kernel_rule(const bap_option* o, int rule) {
 bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units,
                        bool no_events = false) {
     rule = kernel_rule(o, rule);
-    const void* fn = path_fn(o->d, rule, fp64);
+    const void* fn = path_fn(o->d, rule, fp64, o->ppl);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
     size_t smem = path_smem_bytes(a, rule, fp64, o->d);
     if (smem > 227 * 1024 && fp64 && rule != R_NONE) {
@@ -353,6 +355,7 @@ bap_status set_rule_cmc(bap_option* o, int max_stumps) {
 bap_status reserve_items(bap_option* o, int n, int C, int max_iter) {
     const int d = o->d;
     TRY(o->start.reserve((size_t)n * d * 8));
+    TRY(o->l0f.reserve((size_t)n * d * 4));
     TRY(o->state.reserve((size_t)n * sizeof(ItemState)));
     TRY(o->pivot.reserve((size_t)n * 4));
     TRY(o->ctr_item.reserve((size_t)n * 4));
@@ -411,6 +414,7 @@ bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int
     if (it >= 0) a.pass_it = it;
     else a.iter_ptr = &o->iterstate.as<IterState>()->iter;
     a.start = o->start.as<double>();
+    a.l0f = o->l0f.as<float>();
     a.ctr_item = o->ctr_item.as<int>();
     a.pivot = o->pivot.as<int>();
     a.partial = o->partial.as<double>();
@@ -448,6 +452,7 @@ bap_status enqueue_newton_coop(bap_option* o, const bap_iz_params* p, int m, int
                           : 5000000000ULL + (unsigned long long)o->n_items *
                                                 (unsigned long long)p->N1 * (unsigned long long)(o->n_dates - m);
     a.start = o->start.as<double>();
+    a.l0f = o->l0f.as<float>();
     a.ctr_item = o->ctr_item.as<int>();
     a.pivot = o->pivot.as<int>();
     a.partial = o->partial.as<double>();
@@ -493,7 +498,8 @@ bap_status enqueue_iz_setup(bap_option* o, const bap_iz_params* p, int m, bool d
     iz_setup_kernel<<<(o->n_items + 127) / 128, 128, 0, st>>>(
         o->dmodel.as<DevModel>(), m, p->J, o->n_bnd, o->korobov_a.as<int>(), o->start.as<double>(),
         o->state.as<ItemState>(), o->pivot.as<int>(), o->active0.as<int>(), count0,
-        o->coef64.as<double>(), o->n_coef, o->degree, o->fitted.as<int>(), p->warm_start);
+        o->coef64.as<double>(), o->n_coef, o->degree, o->fitted.as<int>(), p->warm_start,
+        o->l0f.as<float>());
     ++o->launches;
     CU(cudaGetLastError());
     return BAP_OK;
@@ -588,6 +594,7 @@ bap_status build_iz_graph(bap_option* o, const bap_iz_params* p, int chunk, int 
     if (e != cudaSuccess) return fail(BAP_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     o->graph_exec = ex;
     o->graph_params = *p;
+    o->graph_chunk = chunk;
     return BAP_OK;
 }
 
@@ -744,9 +751,11 @@ bap_status preload_kernels(int device) {
             for (int rule : {(int)R_NONE, (int)R_IZ, (int)R_CMC, R_NEWTON_COOP, R_IZ3, R_NEWTON_COOP3}) {
                 const bool coop = rule == R_NEWTON_COOP || rule == R_NEWTON_COOP3;
                 for (int fp64 = 0; fp64 < (coop ? 1 : 2); ++fp64) {
-                    const void* fn = path_fn(D, rule, fp64 != 0);
-                    if (!fn) continue;            // no cubic kernels above MAXD_CUBIC
-                    TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+                    for (int ppl = 1; ppl <= 2; ++ppl) {
+                        const void* fn = path_fn(D, rule, fp64 != 0, ppl);
+                        if (!fn) continue;        // no cubic kernels above MAXD_CUBIC
+                        TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+                    }
                 }
             }
         }
@@ -926,7 +935,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     const int J = p->J;
     const int n = o->n_bnd * J;
     o->n_items = n;
-    const int chunk = choose_chunk(n, p->N1);
+    const int chunk = choose_chunk(n, p->N1, o->unit_paths);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     TRY(reserve_items(o, n, C, p->max_iter));
     TRY(o->korobov_a.reserve(8));
@@ -936,7 +945,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     TRY(o->diag_st.reserve((size_t)(o->n_dates + 1) * n * 4));
     cudaStream_t st = o->stream;
     bool use_graph = o->launch_mode == LAUNCH_GRAPH && !o->graph_failed && !o->profiling;
-    if (use_graph && (!o->graph_exec || !same_iz(o->graph_params, *p))) {
+    if (use_graph && (!o->graph_exec || !same_iz(o->graph_params, *p) || o->graph_chunk != chunk)) {
         if (o->graph_exec) {
             cudaGraphExecDestroy(o->graph_exec);
             o->graph_exec = nullptr;
@@ -1172,7 +1181,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     const int J = p->J;
     const int n = J;
     o->n_items = n;
-    const int chunk = choose_chunk(n, p->N2);
+    const int chunk = choose_chunk(n, p->N2, o->unit_paths);
     const int C = (int)((p->N2 + chunk - 1) / chunk);
     const int d = o->d;
     TRY(reserve_items(o, n, C, 1));
@@ -1380,6 +1389,21 @@ bap_status bap_set_wait_limit(bap_option* o, uint64_t ns) {
     return BAP_OK;
 }
 
+bap_status bap_set_unit_paths(bap_option* o, int paths) {
+    clear_error();
+    if (!o || paths < 0 || paths > 65536 || paths % 32 != 0)
+        return fail(BAP_EINVAL, "unit paths must be 0 or a multiple of 32 up to 65536");
+    o->unit_paths = paths;
+    return BAP_OK;
+}
+
+bap_status bap_set_paths_per_lane(bap_option* o, int ppl) {
+    clear_error();
+    if (!o || ppl < 1 || ppl > 2) return fail(BAP_EINVAL, "paths per lane outside 1..2");
+    o->ppl = ppl;
+    return BAP_OK;
+}
+
 bap_status bap_set_boost_form(bap_option* o, int form) {
     if (!o) return fail(BAP_EINVAL, "null option");
     if (form < 0 || form > 3) return fail(BAP_EINVAL, "boost form outside 0..3");
@@ -1496,7 +1520,7 @@ bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_
     AllocScope scope(o->stream);
     cudaStream_t st = o->stream;
     const int n_bnd = (o->payoff == BAP_MAX_CALL && d > 1) ? d : 1;
-    const int chunk = choose_chunk(n_items, p->N1);
+    const int chunk = choose_chunk(n_items, p->N1, o->unit_paths);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     TRY(reserve_items(o, n_items, C, p->max_iter));
     DevBuf ds, dp, di, dl;
@@ -1517,7 +1541,7 @@ bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_
         o->dmodel.as<DevModel>(), m, n_items, n_bnd, ds.as<double>(), dp.as<int>(), di.as<int>(),
         o->start.as<double>(), o->state.as<ItemState>(), o->pivot.as<int>(), o->ctr_item.as<int>(),
         dl.as<int>(), warm ? o->coef64.as<double>() : nullptr, o->n_coef, o->degree,
-        o->fitted.as<int>(), warm ? 1 : 0);
+        o->fitted.as<int>(), warm ? 1 : 0, o->l0f.as<float>());
     newton_items_list_kernel<<<1, 32, 0, st>>>(dl.as<int>(), n_items, o->active0.as<int>(), o->counts.as<int>());
     CU(cudaGetLastError());
     // the fit's own Newton launches, on these items (the option's fit diagnostics stay as they are)

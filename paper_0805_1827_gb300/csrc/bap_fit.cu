@@ -159,10 +159,15 @@ __device__ bool newton_item_init(const DevModel* M, int m, int n_bnd, int b, int
     return live;
 }
 
+// (float) log2 of an item's start point, the form the FP32 path kernels read (l0f).
+__device__ inline void store_log_start(const double* S, int d, float* l0f) {
+    for (int q = 0; q < d; ++q) l0f[q] = (float)log2(S[q]);
+}
+
 __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
                                 double* start, ItemState* state, int* pivot, int* active,
                                 int* count, const double* coef64, int n_coef, int degree,
-                                const int* fitted, int warm_start) {
+                                const int* fitted, int warm_start, float* l0f) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= n_bnd * J) return;
     const int d = M->d;
@@ -184,6 +189,7 @@ __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, cons
                                        warm_start);
     state[item] = st;
     pivot[item] = p;
+    store_log_start(S, d, l0f + (size_t)item * d);
     if (live) {
         const int pos = atomicAdd(count, 1);
         active[pos] = item;
@@ -199,7 +205,7 @@ __global__ void newton_items_setup_kernel(const DevModel* M, int m, int n_items,
                                           const int* ctr_in, double* start, ItemState* state,
                                           int* pivot, int* ctr_item, int* live_flag,
                                           const double* coef64, int n_coef, int degree,
-                                          const int* fitted, int warm_start) {
+                                          const int* fitted, int warm_start, float* l0f) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= n_items) return;
     const int d = M->d;
@@ -213,6 +219,7 @@ __global__ void newton_items_setup_kernel(const DevModel* M, int m, int n_items,
     pivot[item] = p;
     ctr_item[item] = ctr_in[item];
     live_flag[item] = live ? 1 : 0;
+    store_log_start(S, d, l0f + (size_t)item * d);
 }
 
 // Compacts the live items into the first pass's list in index order (one block).
@@ -230,13 +237,10 @@ __global__ void newton_items_list_kernel(const int* live_flag, int n_items, int*
 // quadratic Horner layout [K c_0, for a: c_a, c_ab / K (b = a..s-1)] of B''(S) = K B(S/K) in
 // price units, zero-filled for lower degrees and padded to iz_stage_stride(s + 1) values.
 
-__device__ void stage_iz_one(const double* c, int s, int degree, double K, float* out_f,
+__device__ void stage_iz_one(const double* c, int s, int degree, double K, int p, float* out_f,
                              double* out_d) {
     // x = K B(y/K) with B = sum of c_i times the monomials of y/K: in price units the constant
-    // is K c_0, the linear terms keep c_t, the quadratic c_tu / K, the cubic c_tuv / K^2.  Nested
-    // for Horner: c_0, then for each t: c_t and, for each u >= t, c_tu followed (cubic) by its
-    // c_tuv for v >= u; the evaluation is
-    //   B = c_0 + sum_t y_t (c_t + sum_{u>=t} y_u (c_tu + sum_{v>=u} y_v c_tuv)).
+    // is K c_0, the linear terms keep c_t, the quadratic c_tu / K, the cubic c_tuv / K^2.
     const int stride = iz_stride(s + 1, degree);
     for (int i = 0; i < stride; ++i) { out_f[i] = 0.f; out_d[i] = 0.0; }
     out_f[0] = (float)(K * c[0]);
@@ -249,6 +253,31 @@ __device__ void stage_iz_one(const double* c, int s, int degree, double K, float
         for (int a = 0; a < t; ++a) k += s - a;
         return q0 + k + (u - t);
     };
+    if (degree <= 2) {
+        // Up to quadratic: the polynomial in all d = s + 1 prices, with zero terms for the pivot
+        // asset p, nested for Horner: c_0, then for each asset t: c_t and, for each u >= t, c_tu:
+        //   B = c_0 + sum_t S_t (c_t + sum_{u>=t} c_tu S_u).
+        // The path kernel then evaluates it on the prices as they are, with no reordering.
+        const int d = s + 1;
+        int o = 1;
+        for (int t = 0; t < d; ++t) {
+            const int yt = t < p ? t : t - 1;
+            const double lin = (degree >= 1 && t != p) ? c[1 + yt] : 0.0;
+            out_f[o] = (float)lin;
+            out_d[o] = lin;
+            ++o;
+            for (int u = t; u < d; ++u, ++o) {
+                const int yu = u < p ? u : u - 1;
+                const double q = (degree >= 2 && t != p && u != p) ? c[qpos(yt, yu)] / K : 0.0;
+                out_f[o] = (float)q;
+                out_d[o] = q;
+            }
+        }
+        return;
+    }
+    // Cubic: the polynomial in the d - 1 other prices y (in asset order), nested for Horner:
+    // c_0, then for each t: c_t and, for each u >= t, c_tu followed by its c_tuv for v >= u:
+    //   B = c_0 + sum_t y_t (c_t + sum_{u>=t} y_u (c_tu + sum_{v>=u} y_v c_tuv)).
     auto cpos = [&](int t, int u, int v) { // index of y_t y_u y_v, t <= u <= v
         int k = 0;
         for (int a = 0; a < s; ++a)
@@ -261,21 +290,19 @@ __device__ void stage_iz_one(const double* c, int s, int degree, double K, float
     };
     int o = 1;
     for (int t = 0; t < s; ++t) {
-        const double lin = degree >= 1 ? c[1 + t] : 0.0;
+        const double lin = c[1 + t];
         out_f[o] = (float)lin;
         out_d[o] = lin;
         ++o;
         for (int u = t; u < s; ++u) {
-            const double q = degree >= 2 ? c[qpos(t, u)] / K : 0.0;
+            const double q = c[qpos(t, u)] / K;
             out_f[o] = (float)q;
             out_d[o] = q;
             ++o;
-            if (degree >= 3) {
-                for (int v = u; v < s; ++v, ++o) {
-                    const double cu = c[cpos(t, u, v)] / (K * K);
-                    out_f[o] = (float)cu;
-                    out_d[o] = cu;
-                }
+            for (int v = u; v < s; ++v, ++o) {
+                const double cu = c[cpos(t, u, v)] / (K * K);
+                out_f[o] = (float)cu;
+                out_d[o] = cu;
             }
         }
     }
@@ -286,7 +313,9 @@ __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, in
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (n_dates + 1) * n_bnd) return;
     const size_t so = (size_t)i * iz_stride(s + 1, degree);
-    stage_iz_one(coef64 + (size_t)i * n_coef, s, degree, K, coef_f + so, coef_d + so);
+    const int b = i % n_bnd;
+    stage_iz_one(coef64 + (size_t)i * n_coef, s, degree, K, n_bnd > 1 ? b : 0, coef_f + so,
+                 coef_d + so);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -508,7 +537,7 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
         const size_t o = ((size_t)m * n_bnd + b) * P;
         for (int i = 0; i < P; ++i) coef64[o + i] = coef[i];
         const size_t so = ((size_t)m * n_bnd + b) * iz_stride(d, degree);
-        stage_iz_one(coef64 + o, s, degree, K, coef_f + so, coef_d + so);
+        stage_iz_one(coef64 + o, s, degree, K, p, coef_f + so, coef_d + so);
         if (b == 0) fitted[m] = 1;
     }
 }

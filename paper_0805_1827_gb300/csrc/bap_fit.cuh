@@ -10,13 +10,13 @@ __global__ void korobov_pick_kernel(int J, int s, const double* merit, int* out_
 __global__ void iz_setup_kernel(const DevModel* M, int m, int J, int n_bnd, const int* korobov_a,
                                 double* start, ItemState* state, int* pivot, int* active,
                                 int* count, const double* coef64, int n_coef, int degree,
-                                const int* fitted, int warm_start);
+                                const int* fitted, int warm_start, float* l0f);
 __global__ void newton_items_setup_kernel(const DevModel* M, int m, int n_items, int n_bnd,
                                           const double* starts_in, const int* pivots_in,
                                           const int* ctr_in, double* start, ItemState* state,
                                           int* pivot, int* ctr_item, int* live_flag,
                                           const double* coef64, int n_coef, int degree,
-                                          const int* fitted, int warm_start);
+                                          const int* fitted, int warm_start, float* l0f);
 __global__ void newton_items_list_kernel(const int* live_flag, int n_items, int* active, int* count);
 __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, int n_coef, int s,
                                 int degree, double K, float* coef_f, double* coef_d);
@@ -81,6 +81,8 @@ __global__ void collect_points_kernel(const ItemState* state, int n, double* x_o
 __global__ void collect_labels_kernel(const double* label_y, int n, double* x_out, int* it_out,
                                       int* st_out);
 
-template <int D> const void* path_kernel_fn(int rule, bool fp64);
+// The path kernel of d = D for a rule (or kernel selector), FP32 or FP64, with ppl path slots per
+// lane (2 exists for the FP32 quadratic I&Z kernels; otherwise the ppl = 1 kernel is returned).
+template <int D> const void* path_kernel_fn(int rule, bool fp64, int ppl);
 
 }  // namespace bap

@@ -119,7 +119,7 @@ struct bap_option {
     int method = -1;              // last fit: 0 I&Z, 1 CMC
     int n_items = 0;
     bap::DevBuf start, state, pivot, ctr_item, active0, active1, counts, work, partial,
-        partial_steps, done, total_steps, korobov_a, merit, label_y, label, sorted_v, sorted_i,
+        partial_steps, done, total_steps, l0f, korobov_a, merit, label_y, label, sorted_v, sorted_i,
         err, out_sums, out_steps, out_sums64, out_steps64, trace_tau, trace_phi, diag_x, diag_it,
         diag_st, stat_counts, one, iterstate, bridge_w, check_buf;
     int last_noconv = 0, last_noroot = 0;
@@ -146,9 +146,12 @@ struct bap_option {
     int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device
     unsigned long long wait_limit_ns = 0;   // grid-barrier wait bound; 0: automatic
     int boost_form = 3;           // CMC boosting: 3 by J, 2 warp per feature, 1 cluster, 0 one block
+    int ppl = 1;                  // path slots per lane of the FP32 quadratic I&Z kernels
+    int unit_paths = 0;           // paths per warp unit of the fits' path launches (0: automatic)
     int last_boost_form = 0;      // form the last CMC fit ran
     cudaGraphExec_t graph_exec = nullptr;
     bap_iz_params graph_params{};
+    int graph_chunk = 0;          // unit size the graph was built with
     int graph_failed = 0;
     int last_graph = 0;
 
@@ -156,7 +159,7 @@ struct bap_option {
         bap::DevBuf* all[] = {&dmodel, &s0buf, &fitted, &coef64, &coef_f, &coef_d, &n_stumps,
                               &feat, &thr, &pol, &alpha, &rec_f, &rec_d, &start, &state, &pivot,
                               &ctr_item, &active0, &active1, &counts, &work, &partial,
-                              &partial_steps, &done, &total_steps, &korobov_a, &merit, &label_y,
+                              &partial_steps, &done, &total_steps, &l0f, &korobov_a, &merit, &label_y,
                               &label, &sorted_v, &sorted_i, &err, &out_sums, &out_steps,
                               &out_sums64, &out_steps64, &trace_tau, &trace_phi, &diag_x,
                               &diag_it, &diag_st, &stat_counts, &one, &iterstate, &bridge_w,

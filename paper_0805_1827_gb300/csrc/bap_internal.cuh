@@ -145,8 +145,10 @@ template <> struct PathMath<float> {
     // folded into the radius: cos(2 pi u2) = -cos(2 pi (u2 - 1/2)), same for sin.
     __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
                                                       float& z1) {
-        float u1 = __uint_as_float(0x3f800000u | (w0 >> 9)) - 0.99999988079071044921875f;
-        float u2c = __uint_as_float(0x3f800000u | (w1 >> 9)) - 1.5f;
+        // 1 + v 2^-23 as a bit pattern: the exponent of 1.0 plus the 23-bit v (no carry; an
+        // add of the shifted word, one instruction)
+        float u1 = __uint_as_float((w0 >> 9) + 0x3f800000u) - 0.99999988079071044921875f;
+        float u2c = __uint_as_float((w1 >> 9) + 0x3f800000u) - 1.5f;
         float r = -sqrt_approx(-1.3862943611198906f * lg2_approx(u1));   // -sqrt(-2 ln u1)
         float a = 6.283185307179586f * u2c;
         z0 = r * __cosf(a);
@@ -198,11 +200,12 @@ __host__ __device__ inline int n_basis(int s, int degree) {
     return n;
 }
 
-// Staged I&Z boundary block for the path kernel: always the full quadratic in the d-1 other
-// assets (lower degrees carry zero coefficients), padded to a multiple of 4 values so that a
-// block is read with 16-byte vector loads.
+// Staged I&Z boundary block for the path kernel: always the full quadratic in all d prices,
+// with zero terms for the boundary's pivot asset (lower degrees carry zero coefficients), so
+// that the kernel evaluates it on the prices without reordering them; padded to a multiple of 4
+// values so that a block is read with 16-byte vector loads.
 __host__ __device__ constexpr int iz_stage_stride(int d) {
-    return ((1 + (d - 1) + (d - 1) * d / 2) + 3) & ~3;
+    return ((1 + d + d * (d + 1) / 2) + 3) & ~3;
 }
 
 // The same for a cubic boundary: the full cubic in the d-1 other assets, nested for Horner

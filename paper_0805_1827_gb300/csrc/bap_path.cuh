@@ -46,6 +46,8 @@ struct PathArgs {
     int pass_it;
     const int* iter_ptr;
     double* start;               // items x d start points (FP64); Newton writes the pivot value
+    float* l0f;                  // items x d: (float) log2 of the start points, kept with them by
+                                 // the Newton loop (FP32 kernels; nullptr: taken from start)
     const int* ctr_item;         // Philox counter word 1 per item (nullptr: 0)
     const int* pivot;            // pivot asset per item for the pathwise derivative (or nullptr)
     double* partial;             // items x C x 3
@@ -209,6 +211,7 @@ __device__ inline bool newton_update(const PathArgs& a, int item, double C, doub
     }
     s.x = x;
     S[p] = x;
+    if (a.l0f) a.l0f[(size_t)item * d + p] = (float)log2(x);
     s.done = done ? 1 : 0;
     a.state[item] = s;
     return !done;
@@ -216,18 +219,26 @@ __device__ inline bool newton_update(const PathArgs& a, int item, double C, doub
 
 // ---------------------------------------------------------------------------------------------
 
-// Resident 256-thread blocks per SM the register budget is sized for (no spills at these).
-template <int D, typename Real> constexpr int path_min_blocks() {
-    return sizeof(Real) == 8 ? 2 : (D <= 5 ? 4 : (D <= 9 ? 3 : 2));
+// Resident 256-thread blocks per SM the register budget is sized for (no spills at these),
+// with PPL path slots per lane.
+template <int D, typename Real, int PPL> constexpr int path_min_blocks() {
+    return sizeof(Real) == 8 ? 2 : (PPL > 1 ? (D <= 5 ? 3 : 2) : (D <= 5 ? 4 : (D <= 9 ? 3 : 2)));
 }
 
-// Dynamic shared memory of one launch: the staged rules of dates m+1..NT-1 first (16-byte
-// aligned), then the discount factors, the per-date stepping constants (non-uniform dates
-// only) and the per-date "fitted" flags.
+// Staged rule rows of a launch from date m: dates m+1..NT-1, plus (quadratic I&Z kernels, which
+// evaluate the boundary on every step without a branch) the row of maturity, never used.
+__host__ __device__ inline int staged_rule_rows(int rule, int nk) {
+    return (rule == R_IZ || rule == R_NEWTON_COOP) ? nk : nk - 1;
+}
+
+// Dynamic shared memory of one launch: the staged rule rows first (16-byte aligned), then the
+// discount factors, the per-date stepping constants (non-uniform dates only) and the per-date
+// "fitted" flags.
 inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
     const size_t nk = (size_t)(a.n_dates - a.m);
-    const size_t n = (rule != R_NONE && !a.rules_global ? (nk - 1) * (size_t)a.rule_stride : 0) + nk +
-                     (a.uniform ? 0 : 2 * nk * (size_t)d);
+    const size_t n = (rule != R_NONE && !a.rules_global
+                          ? (size_t)staged_rule_rows(rule, (int)nk) * (size_t)a.rule_stride : 0) +
+                     nk + (a.uniform ? 0 : 2 * nk * (size_t)d);
     return n * (fp64 ? 8 : 4) + nk * sizeof(int);
 }
 
@@ -299,15 +310,15 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* err, un
 // checks that); the barrier's wait is bounded all the same (coop_err, coop_limit_ns).
 // The unit loop is written once, in this kernel body: moved into an inlined device function it
 // compiled measurably slower.
-template <int D, int RULE, typename Real, bool COOP>
-__global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel(const PathArgs a) {
+template <int D, int RULE, typename Real, bool COOP, int PPL = 1>
+__global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NF = D + 1;
     constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
     // rows of dates m+1..NT-1, staged in shared memory (global for an FP64 table too large)
     const bool rules_global = sizeof(Real) == 8 && a.rules_global != 0;
-    const int rule_len = (RULE == R_NONE || rules_global) ? 0 : (nk - 1) * a.rule_stride;
+    const int rule_len = (RULE == R_NONE || rules_global) ? 0 : staged_rule_rows(RULE, nk) * a.rule_stride;
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
     Real* sh_disc = sh_rule + rule_len;
     Real* sh_drift = sh_disc + nk;                   // non-uniform dates: [nk][D]
@@ -375,12 +386,19 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             const int item = active ? __ldcg(active + slot) : slot;
             if (!bap_check(item >= 0 && item < a.n_items, 1, a.checks)) continue;
 
-            // log2 of the start point in FP64, one coordinate per lane, then broadcast
-            const double* st = a.start + (size_t)item * D;
-            const double my_l0 = lane < D ? log2(__ldcg(st + lane)) : 0.0;
+            // log2 of the start point, one coordinate per lane, then broadcast: kept per item by
+            // the Newton loop (the same FP64 log2 rounded to FP32), else taken here in FP64
             Real l0[D];
+            if (sizeof(Real) == 4 && a.l0f != nullptr) {
+                const float my_l0 = lane < D ? __ldcg(a.l0f + (size_t)item * D + lane) : 0.f;
 #pragma unroll
-            for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
+                for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
+            } else {
+                const double* st = a.start + (size_t)item * D;
+                const double my_l0 = lane < D ? log2(__ldcg(st + lane)) : 0.0;
+#pragma unroll
+                for (int q = 0; q < D; ++q) l0[q] = (Real)__shfl_sync(FULL, my_l0, q);
+            }
             const int pivot = a.pivot ? a.pivot[item] : -1;
             // The unit covers paths n_begin .. n_begin + n_count - 1.  Inside the loop only the
             // 32-bit offset nl moves: counter word 0 is (n_begin + nl) mod 2^32 and word 1 stays
@@ -390,114 +408,126 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
             const uint32_t w0_base = (uint32_t)n_begin;
             const uint32_t w1_word = (a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u) + (uint32_t)(n_begin >> 32);
 
-            int nl = lane;
-            bool has = nl < n_count;
-            int next = 32;
-            Real l[D];
+            // PPL path slots per lane: slot s of lane L starts with path s * 32 + L; a slot whose
+            // path stops takes the next path index of the unit (slot-major order across the warp,
+            // by ballot), so early-stopped paths leave no idle slots.  Several slots give the
+            // scheduler independent instruction streams within one warp.
+            int nl[PPL], k[PPL];
+            bool has[PPL];
+            Real l[PPL][D];
 #pragma unroll
-            for (int q = 0; q < D; ++q) l[q] = l0[q];
-            int k = a.m;
+            for (int s = 0; s < PPL; ++s) {
+                nl[s] = s * 32 + lane;
+                has[s] = nl[s] < n_count;
+                k[s] = a.m;
+#pragma unroll
+                for (int q = 0; q < D; ++q) l[s][q] = l0[q];
+            }
+            int next = 32 * PPL;
             Real acc0 = 0, acc1 = 0, acc2 = 0;
             double s0 = 0, s1 = 0, s2 = 0;
             int steps = 0;
 
             // Blocks of up to 32 warp steps; the FP32 partial sums move to FP64 after each block
-            // (a lane ends at most 32 paths in between).  The flush sits outside the inner loop on
-            // purpose: inside it the compiler would evaluate it speculatively on every step, and the
-            // FP64 pipe runs at 1/64 of the FP32 rate.
+            // (a lane ends at most 32 PPL paths in between).  The flush sits outside the inner loop
+            // on purpose: inside it the compiler would evaluate it speculatively on every step, and
+            // the FP64 pipe runs at 1/64 of the FP32 rate.
             bool live = true;
             while (live) {
             for (int it = 0; it < 32; ++it) {
-                live = __any_sync(FULL, has);
+                bool any_has = false;
+#pragma unroll
+                for (int s = 0; s < PPL; ++s) any_has = any_has || has[s];
+                live = __any_sync(FULL, any_has);
                 if (!live) break;
-                bool finished = false;
-                if (has) {
-                    k += 1;
-                    ++steps;
+                bool finished[PPL];
+                // The step of every slot, without a branch: a slot with no path left steps a
+                // throw-away path from date m (so that every index stays in range) and none of
+                // its results count.
+#pragma unroll
+                for (int s = 0; s < PPL; ++s) {
+                    k[s] = has[s] ? k[s] + 1 : a.m + 1;
+                    steps += has[s] ? 1 : 0;
+                    const int ks = k[s];
                     Real z[D];
-                    normals<D, Real>(w0_base + (uint32_t)nl, w1_word, (uint32_t)k, a.rk, z);
+                    normals<D, Real>(w0_base + (uint32_t)nl[s], w1_word, (uint32_t)ks, a.rk, z);
                     if (a.uniform) {
+                        // l_q += drift_q + sum_j L'_qj z_j (L' the vol-scaled factor), the drift
+                        // taken as the first term of the sum
 #pragma unroll
                         for (int q = 0; q < D; ++q) {
-                            Real wq = 0;
+                            Real wq = drift_c(q);
 #pragma unroll
                             for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
-                            l[q] = l[q] + drift_c(q) + wq;
+                            l[s][q] = l[s][q] + wq;
                         }
                     } else {
-                        const int kk = (k - a.m - 1) * D;
+                        const int kk = (ks - a.m - 1) * D;
 #pragma unroll
                         for (int q = 0; q < D; ++q) {
                             Real wq = 0;
 #pragma unroll
                             for (int j = 0; j <= q; ++j) wq = fma(Lc(q, j), z[j], wq);
-                            l[q] = fma(sh_vol[kk + q], wq, l[q] + sh_drift[kk + q]);
+                            l[s][q] = fma(sh_vol[kk + q], wq, l[s][q] + sh_drift[kk + q]);
                         }
                     }
                     // prices and payoff
                     Real S[D];
 #pragma unroll
-                    for (int q = 0; q < D; ++q) S[q] = PathMath<Real>::exp2r(l[q]);
+                    for (int q = 0; q < D; ++q) S[q] = PathMath<Real>::exp2r(l[s][q]);
                     int imax = 0;
-                    Real lmax = l[0];
+                    Real lmax = l[s][0];
 #pragma unroll
                     for (int q = 1; q < D; ++q)
-                        if (l[q] > lmax) { lmax = l[q]; imax = q; }
+                        if (l[s][q] > lmax) { lmax = l[s][q]; imax = q; }
                     Real phi;
                     Real gval = 0;
+                    Real sp;                 // the price tested against the boundary
                     if (is_max) {
-                        Real smax = S[0];
-#pragma unroll
-                        for (int q = 1; q < D; ++q) smax = (q == imax) ? S[q] : smax;
-                        phi = smax - K;
+                        sp = PathMath<Real>::exp2r(lmax);      // = S[imax], the same operation
+                        phi = sp - K;
                     } else if (is_put) {
                         Real b = 0;
 #pragma unroll
                         for (int q = 0; q < D; ++q) b = fma((Real)a.wf[q], S[q], b);
                         phi = K - b;
+                        sp = S[0];
                     } else {
                         Real lg = 0;
 #pragma unroll
-                        for (int q = 0; q < D; ++q) lg = fma((Real)a.wf[q], l[q], lg);
+                        for (int q = 0; q < D; ++q) lg = fma((Real)a.wf[q], l[s][q], lg);
                         gval = PathMath<Real>::exp2r(lg);
                         phi = gval - K;
+                        sp = S[0];
                     }
+                    const int kr = ks - a.m - 1;
+                    bap_check(kr >= 0 && kr < a.n_dates - a.m, 5, a.checks);
+                    const bool at_T = ks == a.n_dates;
                     bool ex = phi > 0;
-                    if (ex && k < a.n_dates) {
-                        const int kr = k - a.m - 1;
-                        bap_check(kr >= 0 && kr < a.n_dates - a.m - 1, 5, a.checks);
+                    if constexpr (RULE == R_IZ) {
+                        // exercise iff S_p passes B_p(S), the pivot p = argmax for the max-call;
+                        // evaluated on every step without a branch (the staged table has a zero
+                        // row for maturity, where only the payoff decides)
+                        Real cc[P4];
+                        load_vec<P4>(rule_rows + kr * a.rule_stride + (is_max ? imax : 0) * P4, cc);
+                        Real B = cc[0];
+                        int idx = 1;
+#pragma unroll
+                        for (int t = 0; t < D; ++t) {
+                            Real acc = cc[idx++];
+#pragma unroll
+                            for (int u = t; u < D; ++u) acc = fma(cc[idx++], S[u], acc);
+                            B = fma(acc, S[t], B);
+                        }
+                        const bool exr = is_put ? (sp <= B) : (sp >= B);
+                        ex = ex && (at_T || (sh_fit[kr] != 0 && exr));
+                    } else if (ex && !at_T) {
                         if (RULE == R_NONE || !sh_fit[kr]) {
                             ex = false;
-                        } else if (RULE == R_IZ) {
-                            // exercise iff S_p passes B''(S_{-p}) (full quadratic, Horner order)
+                        } else if (RULE == R_IZ3) {
+                            // the cubic boundary in the d-1 other prices (nested Horner order);
+                            // the coefficients are read from shared memory as they are used
                             const int p = is_max ? imax : 0;
-                            Real sp = S[0];
-#pragma unroll
-                            for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
-                            Real cc[P4];
-                            load_vec<P4>(rule_rows + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4, cc);
-                            Real B = cc[0];
-                            if constexpr (D > 1) {
-                                Real y[D - 1];
-#pragma unroll
-                                for (int t = 0; t < D - 1; ++t) y[t] = (t < p) ? S[t] : S[t + 1];
-                                int idx = 1;
-#pragma unroll
-                                for (int t = 0; t < D - 1; ++t) {
-                                    Real acc = cc[idx++];
-#pragma unroll
-                                    for (int u = t; u < D - 1; ++u) acc = fma(cc[idx++], y[u], acc);
-                                    B = fma(acc, y[t], B);
-                                }
-                            }
-                            ex = is_put ? (sp <= B) : (sp >= B);
-                    } else if (RULE == R_IZ3) {
-                            // the same test with a cubic boundary (nested Horner order); the
-                            // coefficients are read from shared memory as they are used
-                            const int p = is_max ? imax : 0;
-                            Real sp = S[0];
-#pragma unroll
-                            for (int q = 1; q < D; ++q) sp = (q == p) ? S[q] : sp;
                             const Real* cc = rule_rows + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4;
                             Real B = cc[0];
                             if constexpr (D > 1) {
@@ -519,7 +549,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                                 }
                             }
                             ex = is_put ? (sp <= B) : (sp >= B);
-                    } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
+                        } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
                             const Real* rec = rule_rows + kr * a.rule_stride;
                             Real F = rec[0];
 #pragma unroll
@@ -547,50 +577,52 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real>())) path_kernel
                             ex = F > 0;
                         }
                     }
-                    if (ex || k == a.n_dates) {
-                        finished = true;
-                        Real v = 0, dv = 0;
-                        if (ex) {
-                            const Real disc = sh_disc[k - a.m - 1];
-                            v = disc * phi;
-                            if (pivot >= 0) {
-                                if (is_max) {
-                                    dv = (imax == pivot) ? disc * (phi + K) : (Real)0;
-                                } else if (is_put) {
-                                    Real sp = S[0], wp = (Real)a.wf[0];
+                    ex = ex && has[s];
+                    finished[s] = has[s] && (ex || at_T);
+                    // discounted payoff of a path that stops here (0 if it is not exercised) and
+                    // its pathwise derivative with respect to the pivot's start value
+                    const Real disc = sh_disc[kr];
+                    const Real v = ex ? disc * phi : (Real)0;
+                    Real dv = 0;
+                    if (pivot >= 0) {
+                        if (is_max) {
+                            dv = (imax == pivot) ? disc * (phi + K) : (Real)0;
+                        } else if (is_put) {
+                            Real spv = S[0], wp = (Real)a.wf[0];
 #pragma unroll
-                                    for (int q = 1; q < D; ++q) {
-                                        sp = (q == pivot) ? S[q] : sp;
-                                        wp = (q == pivot) ? (Real)a.wf[q] : wp;
-                                    }
-                                    dv = -disc * wp * sp;
-                                } else {
-                                    Real wp = (Real)a.wf[0];
+                            for (int q = 1; q < D; ++q) {
+                                spv = (q == pivot) ? S[q] : spv;
+                                wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                            }
+                            dv = -disc * wp * spv;
+                        } else {
+                            Real wp = (Real)a.wf[0];
 #pragma unroll
-                                    for (int q = 1; q < D; ++q) wp = (q == pivot) ? (Real)a.wf[q] : wp;
-                                    dv = disc * wp * gval;
-                                }
-                            }
+                            for (int q = 1; q < D; ++q) wp = (q == pivot) ? (Real)a.wf[q] : wp;
+                            dv = disc * wp * gval;
                         }
-                        if (a.mode == MODE_TRACE) {
-                            if (bap_check(n_begin + nl < a.N, 3, a.checks)) {
-                                a.trace_tau[n_begin + nl] = ex ? k : a.n_dates + 1;
-                                a.trace_phi[n_begin + nl] = (double)v;
-                            }
-                        }
-                        acc0 += v;
-                        acc1 += v * v;
-                        acc2 += dv;
+                        dv = ex ? dv : (Real)0;
                     }
+                    if (a.mode == MODE_TRACE && finished[s]) {
+                        if (bap_check(n_begin + nl[s] < a.N, 3, a.checks)) {
+                            a.trace_tau[n_begin + nl[s]] = ex ? ks : a.n_dates + 1;
+                            a.trace_phi[n_begin + nl[s]] = (double)v;
+                        }
+                    }
+                    acc0 += v;
+                    acc1 += v * v;
+                    acc2 += dv;
                 }
-                const unsigned need = __ballot_sync(FULL, finished);
-                if (need) {
-                    if (finished) {
-                        nl = next + __popc(need & lanemask_lt);
-                        has = nl < n_count;
+                // stopped paths take the next path indices of the unit, slot by slot
 #pragma unroll
-                        for (int q = 0; q < D; ++q) l[q] = l0[q];
-                        k = a.m;
+                for (int s = 0; s < PPL; ++s) {
+                    const unsigned need = __ballot_sync(FULL, finished[s]);
+                    if (finished[s]) {
+                        nl[s] = next + __popc(need & lanemask_lt);
+                        has[s] = nl[s] < n_count;
+#pragma unroll
+                        for (int q = 0; q < D; ++q) l[s][q] = l0[q];
+                        k[s] = a.m;
                     }
                     next += __popc(need);
                 }
