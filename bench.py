@@ -41,12 +41,24 @@ WORKLOAD = "5-asset max-call Bermudan, I&Z, rho=0.3, J=1024 Korobov, N1=1e5, 9 d
 CPU_J, CPU_N1, CPU_NPRICE = 64, 4000, 100_000
 
 
+def survey_ops_per_path_step(d: int = 5) -> dict:
+    """Algorithmic 32-bit lane operations of one path-step of the I&Z max-call path, counted
+    by component: Philox4x32-10 at ceil(d/4) calls of 10 rounds x (2 mul-hi + 2 mul-lo + 2
+    xor) plus the key schedule's bumps (80 per call), Box-Muller at 4 MUFU + 6 FP32 per pair,
+    mixing and the log update at d(d+1)/2 + d FMA, the payoff's exp, the quadratic boundary at
+    (d-1)d/2 + d FMA, and the counters, uniforms, argmax and stop test; in total, for d = 5,
+    about 200 integer + 65 FP32 + 13 MUFU = 278 operations."""
+    if d != 5:
+        raise ValueError("the stated total is for d = 5")
+    return {"int": 200, "fp32": 65, "mufu": 13, "total": 278}
+
+
 def alg_ops_per_path_step(d: int = 5, degree: int = 2) -> dict:
-    """Algorithmic 32-bit lane operations of one path-step of the I&Z max-call path:
-    Philox4x32-10: ceil(d/4) calls x 10 rounds x (2 wide multiplies + 4 xor);
-    Box-Muller: ceil(d/2) pairs x (4 uniform ops + 4 MUFU + 4 FP32);
-    mixing d(d+1)/2 FMA; log-space step 2d; prices d exp2 (MUFU); argmax 2(d-1);
-    payoff 2; boundary: (d-1) selects + n_coef FMA + 1 compare."""
+    """A stricter count of the same path-step (the key schedule, which the kernel computes
+    once per launch, and the loop's own bookkeeping left out): Philox4x32-10: ceil(d/4) calls x
+    10 rounds x (2 wide multiplies + 4 xor); Box-Muller: ceil(d/2) pairs x (4 uniform ops + 4
+    MUFU + 4 FP32); mixing d(d+1)/2 FMA; log-space step 2d; prices d exp2 (MUFU); argmax
+    2(d-1); payoff 2; boundary: (d-1) selects + n_coef FMA + 1 compare."""
     s = d - 1
     n_coef = 1 + (s if degree >= 1 else 0) + (s * (s + 1) // 2 if degree >= 2 else 0)
     calls = (d + 3) // 4
@@ -274,6 +286,7 @@ def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
     span_plain = time.perf_counter() - t0 - reqs[0].arrival_s
     mismatches = sum(1 for j in range(len(reqs)) if served[j]["price"] != plain[j]["price"])
     steps = sum(v["fit_path_steps"] + v["path_steps"] for v in served.values())
+    fp64 = [abs(v["fp64_delta"]) / v["se"] for v in served.values() if v["se"] > 0]
     return {"workload": f"{len(reqs)} requests, Poisson arrivals (mean 2 ms), d~U{{1..10}}, "
                         "4..50 dates, inner budget log-U[1e4,1e6], mixed payoffs, I&Z/CMC 50/50, "
                         "pricing 1e5 paths",
@@ -283,6 +296,8 @@ def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
                        "server_thread_finish_s": stats["finish_ms"] / 1e3},
             "plain_per_request": summary(list(lat_p.values()), span_plain),
             "results_equal": mismatches == 0, "mismatches": mismatches,
+            "fp64_delta_over_se": {"max": max(fp64) if fp64 else None,
+                                   "median": statistics.median(fp64) if fp64 else None},
             "path_steps": steps}
 
 
@@ -311,6 +326,39 @@ def profiled_traffic():
         return None
 
 
+def continuation_fp64(bap, opt, params, n_sample: int = 64) -> dict:
+    """The FP32 path's error of continuation estimates at the fit's boundary: for a sample of
+    the last fit's boundary points of every date (start point S0 with the pivot asset at the
+    point), the continuation sums under the fitted rules with the paths stepped in FP32 and in
+    FP64 on the same counters (N1 paths each)."""
+    import numpy as np
+    from bap_workloads import PURPOSE_IZ
+    spec = opt.spec
+    rel = []
+    for m in range(1, spec.n_dates):
+        x, _, st = opt.fit_points(m)
+        n_bnd = spec.d
+        J = len(x) // n_bnd
+        sel = np.linspace(0, len(x) - 1, n_sample // (spec.n_dates - 1) + 1).astype(int)
+        sel = sel[st[sel] == 0]
+        starts = np.zeros((len(sel), spec.d))
+        piv = (sel // J).astype(np.int32)
+        for k, i in enumerate(sel):
+            starts[k, :] = spec.S0            # any positive start; the pivot carries the point
+            starts[k, piv[k]] = x[i]
+        g32, _ = opt.debug_continuation(m, PURPOSE_IZ, params.seed, sel, starts, params.N1, piv)
+        g64, _ = opt.debug_continuation(m, PURPOSE_IZ, params.seed, sel, starts, params.N1, piv,
+                                        fp64=True)
+        c32, c64 = g32[:, 0] / params.N1, g64[:, 0] / params.N1
+        rel += list(np.abs(c32 - c64) / np.maximum(np.abs(c64), 1e-12))
+    rel = np.array(rel)
+    return {"estimates": int(rel.size), "rel_diff_max": float(rel.max()),
+            "rel_diff_median": float(np.median(rel)),
+            "sample": (f"{rel.size} start points over all dates of the S0=100 fit: S0 with the "
+                       "pivot asset at a fitted boundary point; N1 paths each, under the fitted "
+                       "rules")}
+
+
 def launch_forms(bap, params, stream) -> dict:
     """The I&Z fit of the S0=100 option in each launch form on the same seeds (identical fits
     and prices): one launch per Newton pass, one graph with conditional loops, one cooperative
@@ -328,7 +376,7 @@ def launch_forms(bap, params, stream) -> dict:
                 best = r
         out[name] = {"fit_ms": best["fit_ms"], "kernel_launches": best["kernel_launches"],
                      "path_launches": best["path_launches"], "price": best["price"],
-                     "se": best["se"]}
+                     "se": best["se"], "fp64_delta": best["fp64_delta"]}
     prices = {v["price"] for v in out.values()}
     out["identical_prices"] = len(prices) == 1
     return out
@@ -357,7 +405,8 @@ def cmc_boost_forms(bap, stream) -> dict:
             if best is None or r["phase_ms"][2] < best["phase_ms"][2]:
                 best = r
         small[name] = {"boost_ms_per_date": best["phase_ms"][2] / (sspec.n_dates - 1),
-                       "fit_ms": best["fit_ms"], "price": best["price"]}
+                       "fit_ms": best["fit_ms"], "price": best["price"], "se": best["se"],
+                       "fp64_delta": best["fp64_delta"]}
     small["identical_prices"] = len({small[k]["price"] for k in names.values()}) == 1
     small["workload"] = "5-asset max-call, CMC, J=1024, N2=200, 200 stumps, 10 fitted dates"
     spec = spec_basket_put_7(0)
@@ -375,7 +424,7 @@ def cmc_boost_forms(bap, stream) -> dict:
             if best is None or r["fit_ms"] < best["fit_ms"]:
                 best = r
         out[name] = {"fit_ms": best["fit_ms"], "price": best["price"], "se": best["se"],
-                     "form_ran": names[best["form_ran"]]}
+                     "fp64_delta": best["fp64_delta"], "form_ran": names[best["form_ran"]]}
     out["identical_prices"] = len({out[k]["price"] for k in names.values()}) == 1
     # LogitBoost (Section 3.2's alternative), 100 rounds = 200 vote stumps, on its cluster kernel
     lp = CMCParams(J=4000, N2=20_000, n_stumps=100, seed=1, boost=1)
@@ -388,7 +437,7 @@ def cmc_boost_forms(bap, stream) -> dict:
         if best is None or r["fit_ms"] < best["fit_ms"]:
             best = r
     out["logitboost_cluster"] = {"fit_ms": best["fit_ms"], "price": best["price"], "se": best["se"],
-                                 "rounds": 100}
+                                 "fp64_delta": best["fp64_delta"], "rounds": 100}
     out["workload"] = "7-asset basket put, CMC, J=4000, N2=2e4, 200 stumps, 9 fitted dates"
     return out
 
@@ -409,7 +458,8 @@ def paper_tables(bap) -> dict:
             o.fit_classifier(params)
         r = o.price(1_000_000, 2)
         o.close()
-        return {"price": r["price"], "se": r["se"], "fit_ms": r["fit_ms"], "price_ms": r["price_ms"]}
+        return {"price": r["price"], "se": r["se"], "fp64_delta": r["fp64_delta"],
+                "fit_ms": r["fit_ms"], "price_ms": r["price_ms"]}
 
     out = {"table1_iz": {}, "table2_iz_J": {}, "table3_iz_N1": {}, "table4_cmc": {}}
     for s0 in (90, 100, 110):
@@ -452,7 +502,7 @@ def root_find_study(bap) -> dict:
                      "evals_p90": float(np.percentile(its, 90)), "evals_max": int(its.max()),
                      "points": int(its.size), "noconv": r["n_noconv"],
                      "fit_path_steps": r["fit_path_steps"], "fit_ms": r["fit_ms"],
-                     "price": r["price"], "se": r["se"]}
+                     "price": r["price"], "se": r["se"], "fp64_delta": r["fp64_delta"]}
     return out
 
 
@@ -466,7 +516,8 @@ def boundary_degree_study(bap) -> dict:
             o.fit_boundary(IZParams(J=128, N1=5000, degree=deg, seed=1))
             r = o.price(1_000_000, 2)
             o.close()
-            out[f"S0={s0},degree={deg}"] = {"price": r["price"], "se": r["se"], "fit_ms": r["fit_ms"]}
+            out[f"S0={s0},degree={deg}"] = {"price": r["price"], "se": r["se"],
+                                            "fp64_delta": r["fp64_delta"], "fit_ms": r["fit_ms"]}
     return out
 
 
@@ -571,18 +622,21 @@ def run_ours(args) -> None:
             torch.distributed.destroy_process_group()
         return
 
+    cont64 = continuation_fp64(bap, opts[1], params)
     forms = launch_forms(bap, params, stream) if args.launch_forms else None
     boost = cmc_boost_forms(bap, stream) if args.launch_forms else None
     tables = paper_tables(bap) if args.paper_tables else None
     rootfind = root_find_study(bap) if args.paper_tables else None
     degrees = boundary_degree_study(bap) if args.paper_tables else None
 
-    ops = alg_ops_per_path_step(5, 2)
+    ops = survey_ops_per_path_step(5)
+    strict = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * sm_max * 1e6    # lane-ops/s at max clock
-    achieved = (tot_steps * ops["total"]) / (tot_kms / 1e3) if tot_kms > 0 else None
-    roof = {"bound": "alu", "kernel": "path_kernel<5,IZ,float>",
+    rate = tot_steps / (tot_kms / 1e3) if tot_kms > 0 else None    # path-steps/s in kernel
+    achieved = rate * ops["total"] if rate else None
+    roof = {"bound": "alu", "kernel": "path_kernel<5,IZ,float> (cooperative Newton launch)",
             "achieved": achieved / 1e12 if achieved else None,
             "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": (achieved / peak_ops) if achieved else None,
@@ -590,7 +644,12 @@ def run_ours(args) -> None:
             "traffic_basis": "ncu DRAM read+write bytes per cooperative Newton launch (full "
                              "workload, profiles/path_kernel_5d_max_call.md)",
             "ops_per_path_step": ops["total"],
-            "path_steps_per_s_in_kernel": tot_steps / (tot_kms / 1e3) if tot_kms > 0 else None,
+            "ops_basis": "per d=5 path-step: Philox 2 calls x 80 (incl. key schedule), "
+                         "Box-Muller 3 x (4 MUFU + 6 FP32), mixing 20, payoff 1 exp, boundary 15, "
+                         "counters/uniforms/argmax/stop ~ 52: ~200 int + 65 FP32 + 13 MUFU",
+            "frac_strict": (rate * strict["total"] / peak_ops) if rate else None,
+            "ops_per_path_step_strict": strict["total"],
+            "path_steps_per_s_in_kernel": rate,
             "peak_basis": (f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {sm_max:.0f} "
                            "MHz (issue-slot peak; MEASURED_PEAKS sm_max_mhz)")}
     line = {
@@ -611,6 +670,7 @@ def run_ours(args) -> None:
         "paper_tables": tables,
         "root_find_study": rootfind,
         "boundary_degree_study": degrees,
+        "continuation_fp64": cont64,
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},

@@ -270,6 +270,14 @@ bap_status bap_debug_continuation(bap_option *opt, int m, int purpose, uint64_t 
                                   int n_items, const int *item_ids, const int *pivots,
                                   const double *starts, int64_t N, double *sums, int64_t *steps);
 
+/* The same sums with the paths stepped in FP64 (the kernel of bap_price's FP64 re-run): the
+ * FP32 path's error of a continuation estimate is the difference of the two on the same
+ * counters and rules.  Arguments and errors as bap_debug_continuation. */
+bap_status bap_debug_continuation_fp64(bap_option *opt, int m, int purpose, uint64_t seed,
+                                       int n_items, const int *item_ids, const int *pivots,
+                                       const double *starts, int64_t N, double *sums,
+                                       int64_t *steps);
+
 /* Per-path exercise date (n_dates+1 = never) and discounted payoff of one item (parity hook). */
 bap_status bap_debug_paths(bap_option *opt, int m, int purpose, uint64_t seed, int item_id,
                            const double *start, int64_t N, int *tau, double *disc_phi);

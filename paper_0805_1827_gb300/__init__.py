@@ -34,7 +34,7 @@ EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch
             "bap_debug_checks", "bap_checked_build",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
-            "bap_debug_rng", "bap_debug_newton", "bap_debug_ls_fit", "bap_debug_boost",
+            "bap_debug_rng", "bap_debug_continuation_fp64", "bap_debug_newton", "bap_debug_ls_fit", "bap_debug_boost",
             "bap_destroy", "bap_last_error", "bap_version", "bap_server_create",
             "bap_server_set_launch_mode", "bap_submit", "bap_poll", "bap_wait", "bap_cancel",
             "bap_server_get_stats", "bap_server_destroy"]
@@ -139,6 +139,8 @@ def lib():
         L.bap_fit_points.argtypes = [vp, C.c_int, ip, dp, ip, ip]
         L.bap_debug_continuation.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, C.c_int, ip, ip, dp,
                                              C.c_int64, dp, i64p]
+        L.bap_debug_continuation_fp64.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, C.c_int, ip,
+                                                  ip, dp, C.c_int64, dp, i64p]
         L.bap_debug_paths.argtypes = [vp, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, C.c_int64,
                                       ip, dp]
         L.bap_debug_rng.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.c_int,
@@ -286,16 +288,17 @@ class Option:
         return x, it, st
 
     def debug_continuation(self, m: int, purpose: int, seed: int, item_ids, starts, N: int,
-                           pivots=None):
+                           pivots=None, fp64: bool = False):
+        """Continuation sums (n_items x 3) and path-steps; fp64=True steps the paths in FP64."""
         starts = _f64(np.atleast_2d(starts))
         n = starts.shape[0]
         ids = np.ascontiguousarray(item_ids, dtype=np.int32)
         piv = None if pivots is None else np.ascontiguousarray(pivots, dtype=np.int32)
         sums = np.zeros((n, 3))
         steps = np.zeros(n, dtype=np.int64)
-        _check(lib().bap_debug_continuation(self.h, m, purpose, seed, n, _ip(ids),
-                                            None if piv is None else _ip(piv), _dp(starts), N,
-                                            _dp(sums), steps.ctypes.data_as(C.POINTER(C.c_int64))))
+        fn = lib().bap_debug_continuation_fp64 if fp64 else lib().bap_debug_continuation
+        _check(fn(self.h, m, purpose, seed, n, _ip(ids), None if piv is None else _ip(piv),
+                  _dp(starts), N, _dp(sums), steps.ctypes.data_as(C.POINTER(C.c_int64))))
         return sums, steps
 
     def debug_newton(self, params, m: int, item_ids, pivots, starts, bracket: bool = False):

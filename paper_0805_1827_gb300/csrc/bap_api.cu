@@ -1446,10 +1446,10 @@ bap_status bap_price(bap_option* o, int64_t n_paths, uint64_t seed, bap_result* 
     return finish_price(o, res);
 }
 
-bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t seed, int n_items,
-                                  const int* item_ids, const int* pivots, const double* starts,
-                                  int64_t N, double* sums, int64_t* steps) {
-    clear_error();
+namespace {
+bap_status debug_continuation_impl(bap_option* o, int m, int purpose, uint64_t seed, int n_items,
+                                   const int* item_ids, const int* pivots, const double* starts,
+                                   int64_t N, double* sums, int64_t* steps, bool fp64) {
     if (!o || !item_ids || !starts || !sums || !steps) return fail(BAP_EINVAL, "null argument");
     if (m < 1 || m >= o->n_dates) return fail(BAP_EINVAL, "m=%d outside 1..n_dates-1", m);
     if (n_items < 1 || N < 1 || N > (1LL << 31)) return fail(BAP_EINVAL, "bad n_items or N");
@@ -1469,10 +1469,28 @@ bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t se
     CU(cudaMemcpyAsync(di.p, item_ids, (size_t)n_items * 4, cudaMemcpyHostToDevice, o->stream));
     if (pivots) CU(cudaMemcpyAsync(dp.p, pivots, (size_t)n_items * 4, cudaMemcpyHostToDevice, o->stream));
     std::vector<long long> st(n_items);
-    TRY(run_sums(o, m, MODE_SUMS, false, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), n_items, N,
+    TRY(run_sums(o, m, MODE_SUMS, fp64, make_round_keys(seed, (uint32_t)purpose, (uint32_t)m), n_items, N,
                  di.as<int>(), pivots ? dp.as<int>() : nullptr, ds.as<double>(), sums, st.data()));
     for (int i = 0; i < n_items; ++i) steps[i] = st[i];
     return BAP_OK;
+}
+}  // namespace
+
+bap_status bap_debug_continuation(bap_option* o, int m, int purpose, uint64_t seed, int n_items,
+                                  const int* item_ids, const int* pivots, const double* starts,
+                                  int64_t N, double* sums, int64_t* steps) {
+    clear_error();
+    return debug_continuation_impl(o, m, purpose, seed, n_items, item_ids, pivots, starts, N, sums,
+                                   steps, false);
+}
+
+bap_status bap_debug_continuation_fp64(bap_option* o, int m, int purpose, uint64_t seed,
+                                       int n_items, const int* item_ids, const int* pivots,
+                                       const double* starts, int64_t N, double* sums,
+                                       int64_t* steps) {
+    clear_error();
+    return debug_continuation_impl(o, m, purpose, seed, n_items, item_ids, pivots, starts, N, sums,
+                                   steps, true);
 }
 
 bap_status bap_debug_paths(bap_option* o, int m, int purpose, uint64_t seed, int item_id,

@@ -148,9 +148,10 @@ template <> struct PathMath<float> {
         // 1 + v 2^-23 as a bit pattern: the exponent of 1.0 plus the 23-bit v (no carry; an
         // add of the shifted word, one instruction)
         float u1 = __uint_as_float((w0 >> 9) + 0x3f800000u) - 0.99999988079071044921875f;
-        float u2c = __uint_as_float((w1 >> 9) + 0x3f800000u) - 1.5f;
         float r = -sqrt_approx(-1.3862943611198906f * lg2_approx(u1));   // -sqrt(-2 ln u1)
-        float a = 6.283185307179586f * u2c;
+        // a = 2 pi (u2 - 1/2) from the bit pattern 1 + u2 in one fused multiply-add
+        float a = fmaf(__uint_as_float((w1 >> 9) + 0x3f800000u), 6.283185307179586f,
+                       -9.42477796076938f);
         z0 = r * __cosf(a);
         z1 = r * __sinf(a);
     }

@@ -313,6 +313,8 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* err, un
 template <int D, int RULE, typename Real, bool COOP, int PPL = 1>
 __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // each thread's FP64 partial sums of its unit (kept here rather than in six registers)
+    __shared__ double sh_sum[3][256];
     constexpr int NF = D + 1;
     constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
@@ -425,7 +427,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             }
             int next = 32 * PPL;
             Real acc0 = 0, acc1 = 0, acc2 = 0;
-            double s0 = 0, s1 = 0, s2 = 0;
+            sh_sum[0][threadIdx.x] = 0.0;
+            sh_sum[1][threadIdx.x] = 0.0;
+            sh_sum[2][threadIdx.x] = 0.0;
             int steps = 0;
 
             // Blocks of up to 32 warp steps; the FP32 partial sums move to FP64 after each block
@@ -627,10 +631,13 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                     next += __popc(need);
                 }
             }
-            s0 += (double)acc0; s1 += (double)acc1; s2 += (double)acc2;
+            sh_sum[0][threadIdx.x] += (double)acc0;
+            sh_sum[1][threadIdx.x] += (double)acc1;
+            sh_sum[2][threadIdx.x] += (double)acc2;
             acc0 = acc1 = acc2 = 0;
             }
             long long steps64 = steps;
+            double s0 = sh_sum[0][threadIdx.x], s1 = sh_sum[1][threadIdx.x], s2 = sh_sum[2][threadIdx.x];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 s0 += __shfl_down_sync(FULL, s0, off);
