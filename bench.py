@@ -442,6 +442,45 @@ def cmc_boost_forms(bap, stream) -> dict:
     return out
 
 
+def cmc_ops_per_path_step(d: int, n_stumps: int) -> int:
+    """Algorithmic operations of one CMC label path-step of the d-asset basket put, counted by
+    component: Philox4x32-10 ceil(d/4) calls x 80 (key schedule included), Box-Muller ceil(d/2)
+    pairs x (4 MUFU + 6 FP32), mixing and the log update d(d+1)/2 + d, the basket payoff d exp
+    + d FMA, and the stump rule (d+1) features x (ceil(log2(stumps per feature)) + 1) compares
+    plus d+1 adds."""
+    per_f = max(1, n_stumps // (d + 1))
+    rule = (d + 1) * (math.ceil(math.log2(per_f)) + 1) + (d + 1)
+    return ((d + 3) // 4) * 80 + ((d + 1) // 2) * 10 + d * (d + 1) // 2 + d + 2 * d + rule
+
+
+def cmc_labels_7d(bap, stream, peak_ops: float) -> dict:
+    """The CMC label paths of the 7-asset basket put (sigma_i ~ U[0.15, 0.35], seeded
+    correlation, J = 4000 training points, N2 = 2e4 inner paths, 200 stumps, 9 fitted dates):
+    inner path-steps per second of the [calc] phase (training points and label launches, CUDA
+    events) and its fraction of the issue-slot peak."""
+    from bap_workloads import CMCParams, spec_basket_put_7
+    spec = spec_basket_put_7(0)
+    params = CMCParams(J=4000, N2=20_000, n_stumps=200, seed=1)
+    best = None
+    for rep in range(2):
+        o = bap.Option(spec, stream=stream.cuda_stream)
+        o.set_profiling(True)
+        o.fit_classifier(params)
+        r = o.price(1_000_000, 5)
+        o.close()
+        if best is None or r["phase_ms"][1] < best["phase_ms"][1]:
+            best = r
+    rate = best["fit_path_steps"] / (best["phase_ms"][1] / 1e3)
+    ops = cmc_ops_per_path_step(7, 200)
+    return {"workload": "7-asset basket put, CMC, J=4000, N2=2e4, 200 stumps, 9 fitted dates",
+            "path_steps_per_s": rate, "calc_ms": best["phase_ms"][1],
+            "fit_path_steps": best["fit_path_steps"], "ops_per_path_step": ops,
+            "frac": rate * ops / peak_ops, "fit_ms": best["fit_ms"],
+            "boost_ms_per_date": best["phase_ms"][2] / (spec.n_dates - 1),
+            "price": best["price"], "se": best["se"], "fp64_delta": best["fp64_delta"],
+            "launch": bap.tuned_launch(7, "cmc", 0, 4000, 20_000)}
+
+
 def paper_tables(bap) -> dict:
     """The paper's 3-asset max-call (Eq. 2 / Eq. 3) at its own settings: Table 1 (I&Z, J=128,
     N1=5e3), Table 2 (J sweep), Table 3 (N1 sweep), Table 4 (CMC, 5e3 points, N2=500, 200
@@ -623,6 +662,9 @@ def run_ours(args) -> None:
         return
 
     cont64 = continuation_fp64(bap, opts[1], params)
+    peaks0 = _peaks()
+    peak_issue = props.multi_processor_count * 128 * float(peaks0.get("sm_max_mhz", 2070.0)) * 1e6
+    cmc7 = cmc_labels_7d(bap, stream, peak_issue)
     forms = launch_forms(bap, params, stream) if args.launch_forms else None
     boost = cmc_boost_forms(bap, stream) if args.launch_forms else None
     tables = paper_tables(bap) if args.paper_tables else None
@@ -671,6 +713,10 @@ def run_ours(args) -> None:
         "root_find_study": rootfind,
         "boundary_degree_study": degrees,
         "continuation_fp64": cont64,
+        "cmc_labels_7d": cmc7,
+        "launch_config": {"5-asset I&Z fit": bap.tuned_launch(5, "iz", 2, 5 * J, N1),
+                          "source": "autotuner table compiled into the library "
+                                    "(paper_0805_1827_gb300/csrc/bap_tuning.inc)"},
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
                                   "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
                    for s0, r in zip(S0S, last)},

@@ -204,18 +204,33 @@ bap_status bap_debug_checks(bap_option *opt, uint64_t *count, int *first_code);
 /* 1 in the checked build, 0 in the normal one. */
 int bap_checked_build(void);
 
+/* The launch configuration the library picks for a fit's path launches: for quadratic (or
+ * lower) I&Z fits the autotuner's table entry (measured on the target GPU by autotune.py and
+ * compiled into the library) nearest to (d, n_items points, N inner paths); otherwise a fixed
+ * formula.  It depends on the fit's shape only, so a fit's result is the same alone and served.
+ * *unit_paths = paths per warp unit, *paths_per_lane = path slots per lane, *from_table (may be
+ * NULL) = 1 if a table entry decided.  Errors: EINVAL. */
+bap_status bap_tuned_launch(int d, int method, int degree, int64_t n_items, int64_t N,
+                            int *unit_paths, int *paths_per_lane, int *from_table);
+
+/* Cooperative Newton launches of the option use at most 1/share of the device (1, the default,
+ * the whole device; the serving loop sets min(max_inflight, 8) so that requests overlap).  The
+ * share changes how many blocks run, never the results.  Errors: EINVAL (share outside 1..64). */
+bap_status bap_set_grid_share(bap_option *opt, int share);
+
 /* Paths per warp unit of the fits' path launches (I&Z Newton passes, CMC labels): 0 (default)
- * chooses from the launch shape (about 16k units of 64..2048 paths); else a multiple of 32 up to
- * 65536.  Longer units spread a unit's fixed set-up and reduction over more paths; shorter ones
+ * takes the autotuner's choice for the launch shape (bap_tuned_launch); else a multiple of 32 up
+ * to 65536.  Longer units spread a unit's fixed set-up and reduction over more paths; shorter ones
  * balance passes with few points.  The choice changes how FP32 partial sums are grouped, so
  * results differ between settings by rounding only.  Errors: EINVAL. */
 bap_status bap_set_unit_paths(bap_option *opt, int paths);
 
-/* Path slots per lane of the FP32 kernels with a quadratic (or lower) I&Z boundary: 1 (default)
- * or 2.  With 2, every lane advances two paths per step, interleaved, which gives the warp
- * schedulers more independent work; the kernel runs fewer resident blocks.  The choice changes
- * how FP32 partial sums are grouped, so results differ from the other setting by rounding only.
- * Errors: EINVAL (null option, ppl outside 1..2). */
+/* Path slots per lane of the FP32 kernels with a quadratic (or lower) I&Z boundary: 0 (default)
+ * takes the autotuner's choice for the fit's Newton launches (1 elsewhere); 1 or 2 forces it.
+ * With 2, every lane advances two paths per step, interleaved, which gives the warp schedulers
+ * more independent work; the kernel runs fewer resident blocks.  The choice changes how FP32
+ * partial sums are grouped, so results differ between settings by rounding only.
+ * Errors: EINVAL (null option, ppl outside 0..2). */
 bap_status bap_set_paths_per_lane(bap_option *opt, int ppl);
 
 /* How bap_fit_classifier runs the AdaBoost of each date ([class], Section 3.2; the paper's

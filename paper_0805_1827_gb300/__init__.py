@@ -30,7 +30,8 @@ MAX_D, MAX_DATES, MAX_STUMPS = 10, 64, 256
 
 EXPORTED = ["bap_create", "bap_set_stream", "bap_set_profiling", "bap_set_launch_mode",
             "bap_set_boost_form", "bap_last_boost_form", "bap_set_wait_limit",
-            "bap_set_paths_per_lane", "bap_set_unit_paths",
+            "bap_set_paths_per_lane", "bap_set_unit_paths", "bap_tuned_launch",
+            "bap_set_grid_share",
             "bap_debug_checks", "bap_checked_build",
             "bap_fit_boundary", "bap_fit_classifier", "bap_price", "bap_export_rules",
             "bap_import_rules", "bap_fit_points", "bap_debug_continuation", "bap_debug_paths",
@@ -117,6 +118,8 @@ def lib():
         L.bap_set_boost_form.argtypes = [vp, C.c_int]
         L.bap_set_paths_per_lane.argtypes = [vp, C.c_int]
         L.bap_set_unit_paths.argtypes = [vp, C.c_int]
+        L.bap_tuned_launch.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int64, C.c_int64, ip, ip, ip]
+        L.bap_set_grid_share.argtypes = [vp, C.c_int]
         L.bap_set_wait_limit.argtypes = [vp, C.c_uint64]
         L.bap_debug_checks.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int)]
         L.bap_checked_build.argtypes = []
@@ -238,6 +241,9 @@ class Option:
 
     def set_wait_limit(self, ns: int):
         _check(lib().bap_set_wait_limit(self.h, ns))
+
+    def set_grid_share(self, share: int):
+        _check(lib().bap_set_grid_share(self.h, share))
 
     def set_unit_paths(self, paths: int):
         _check(lib().bap_set_unit_paths(self.h, paths))
@@ -423,6 +429,14 @@ def debug_rng(seed: int, purpose: int, m: int, w1: int, step: int, d: int, count
     _check(lib().bap_debug_rng(seed, purpose, m, w1, step, d, count,
                                words.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(z)))
     return words, z
+
+
+def tuned_launch(d: int, method: str, degree: int, n_items: int, N: int) -> dict:
+    """The launch configuration the library picks for a fit's path launches of this shape."""
+    u, p, t = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(lib().bap_tuned_launch(d, METHOD_CODE[method], degree, n_items, N, C.byref(u),
+                                  C.byref(p), C.byref(t)))
+    return {"unit_paths": u.value, "paths_per_lane": p.value, "from_table": bool(t.value)}
 
 
 def version() -> str:

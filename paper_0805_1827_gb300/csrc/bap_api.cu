@@ -169,6 +169,52 @@ int choose_chunk(long long n_items, long long N, int unit_paths = 0) {
     return (int)c;
 }
 
+// ---- launch configuration from the autotuner's table ------------------------------------------
+// bap_tuning.inc holds, per launch shape measured on the target GPU by the project's autotuner
+// (autotune.py), the fastest paths per warp unit and path slots per lane of the quadratic I&Z
+// Newton launches: entries {d, kind 0, items, N, unit paths, slots per lane}.  A fit takes the
+// entry of its d nearest to its shape (log distance in items and paths); without one, the fixed
+// formula of choose_chunk and one slot per lane.
+struct TuneEntry {
+    int d, kind, items;
+    long long N;
+    int unit, ppl;
+};
+const TuneEntry kTune[] = {
+#include "bap_tuning.inc"
+    {0, -1, 0, 0, 0, 0}};
+
+struct LaunchChoice {
+    int unit = 0;         // 0: the formula
+    int ppl = 1;
+    bool tuned = false;
+};
+
+LaunchChoice tuned_launch(int d, int kind, long long n_items, long long N) {
+    LaunchChoice c;
+    double best = 1e300;
+    for (const TuneEntry& e : kTune) {
+        if (e.kind != kind || e.d != d || e.items <= 0 || e.N <= 0) continue;
+        const double dist = std::fabs(std::log((double)n_items / e.items)) +
+                            std::fabs(std::log((double)N / (double)e.N));
+        if (dist < best) {
+            best = dist;
+            c.unit = e.unit;
+            c.ppl = e.ppl;
+            c.tuned = true;
+        }
+    }
+    return c;
+}
+
+// The tuning kind of a fit: 0 the quadratic (or lower) I&Z Newton launches; the other launches
+// (-1: cubic boundaries, CMC labels) take the formula.  The choice depends on the fit's shape
+// only, never on what else runs or on the device share, so a fit's result is the same alone
+// and served.
+int tune_kind(int method, int degree) {
+    return (method == BAP_METHOD_IZ && degree <= 2) ? 0 : -1;
+}
+
 // The kernel for a rule: a cubic I&Z boundary has kernels of its own.
 int kernel_rule(const bap_option* o, int rule) {
     if (o->rule_kind == R_IZ && o->degree >= 3) {
@@ -182,16 +228,26 @@ int kernel_rule(const bap_option* o, int rule) {
 bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long long max_units,
                        bool no_events = false) {
     rule = kernel_rule(o, rule);
-    const void* fn = path_fn(o->d, rule, fp64, o->ppl);
+    // path slots per lane: the option's setting, else the tuned choice of the fit's Newton launches
+    const int ppl = o->ppl ? o->ppl : (a.mode == MODE_NEWTON ? o->ppl_fit : 1);
+    const void* fn = path_fn(o->d, rule, fp64, ppl);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
+    // the dynamic shared memory the kernel may use (the device's limit less its static arrays)
+    size_t max_smem = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_fn_mu);
+        FnInfo& fi = g_fn[{fn, o->device}];
+        TRY(raise_smem_limit(fn, o->device, fi));
+        max_smem = fi.max_dyn_smem;
+    }
     size_t smem = path_smem_bytes(a, rule, fp64, o->d);
-    if (smem > 227 * 1024 && fp64 && rule != R_NONE) {
+    if (smem > max_smem && fp64 && rule != R_NONE) {
         // the FP64 re-run of a table too large to stage (many dates, many coefficients or
         // stumps): its kernel reads the rule rows from global memory instead
         a.rules_global = 1;
         smem = path_smem_bytes(a, rule, fp64, o->d);
     }
-    if (smem > 227 * 1024) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
+    if (smem > max_smem) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps = 1;
     TRY(path_blocks_per_sm(fn, o->device, smem, &bps));
     long long blocks = (max_units + (kBlock / 32) - 1) / (kBlock / 32);
@@ -935,8 +991,11 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     const int J = p->J;
     const int n = o->n_bnd * J;
     o->n_items = n;
-    const int chunk = choose_chunk(n, p->N1, o->unit_paths);
+    const LaunchChoice lc = tuned_launch(o->d, tune_kind(BAP_METHOD_IZ, p->degree), n, p->N1);
+    const int chunk = choose_chunk(n, p->N1, o->unit_paths ? o->unit_paths : lc.unit);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
+    o->ppl_fit = lc.ppl;
+    o->last_unit = chunk;
     TRY(reserve_items(o, n, C, p->max_iter));
     TRY(o->korobov_a.reserve(8));
     TRY(o->merit.reserve((size_t)(J + 1) * 8));
@@ -1181,7 +1240,9 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     const int J = p->J;
     const int n = J;
     o->n_items = n;
-    const int chunk = choose_chunk(n, p->N2, o->unit_paths);
+    const LaunchChoice lc = tuned_launch(o->d, tune_kind(BAP_METHOD_CMC, 0), n, p->N2);
+    const int chunk = choose_chunk(n, p->N2, o->unit_paths ? o->unit_paths : lc.unit);
+    o->last_unit = chunk;
     const int C = (int)((p->N2 + chunk - 1) / chunk);
     const int d = o->d;
     TRY(reserve_items(o, n, C, 1));
@@ -1313,13 +1374,17 @@ size_t estimate_bytes(const bap_model* md, int method, const void* params, int64
         const bap_iz_params* p = static_cast<const bap_iz_params*>(params);
         const size_t nb = (md->payoff == BAP_MAX_CALL && md->d > 1) ? d : 1;
         n = nb * (size_t)p->J;
-        C = (size_t)((p->N1 + choose_chunk((long long)n, p->N1) - 1) / choose_chunk((long long)n, p->N1));
+        const int u = choose_chunk((long long)n, p->N1,
+                                   tuned_launch(md->d, tune_kind(BAP_METHOD_IZ, p->degree), (long long)n, p->N1).unit);
+        C = (size_t)((p->N1 + u - 1) / u);
         extra = (size_t)(p->J + 1) * 8 + (size_t)(p->max_iter + 2) * 12;
         rules = nd * nb * (size_t)(MAXCOEF + 4) * 20;
     } else {
         const bap_cmc_params* p = static_cast<const bap_cmc_params*>(params);
         n = (size_t)p->J;
-        C = (size_t)((p->N2 + choose_chunk((long long)n, p->N2) - 1) / choose_chunk((long long)n, p->N2));
+        const int u = choose_chunk((long long)n, p->N2,
+                                   tuned_launch(md->d, tune_kind(BAP_METHOD_CMC, 0), (long long)n, p->N2).unit);
+        C = (size_t)((p->N2 + u - 1) / u);
         extra = (d + 1) * n * 20 + d * n * 8;     // sorted features, bridge state
         rules = nd * (size_t)p->n_stumps * (p->boost == 1 ? 2 : 1) * 64;
     }
@@ -1389,6 +1454,25 @@ bap_status bap_set_wait_limit(bap_option* o, uint64_t ns) {
     return BAP_OK;
 }
 
+bap_status bap_tuned_launch(int d, int method, int degree, int64_t n_items, int64_t N,
+                            int* unit_paths, int* paths_per_lane, int* from_table) {
+    clear_error();
+    if (!unit_paths || !paths_per_lane || d < 1 || d > MAXD || n_items < 1 || N < 1)
+        return fail(BAP_EINVAL, "bad argument");
+    const LaunchChoice lc = tuned_launch(d, tune_kind(method, degree), n_items, N);
+    *unit_paths = choose_chunk(n_items, N, lc.unit);
+    *paths_per_lane = lc.ppl;
+    if (from_table) *from_table = lc.tuned ? 1 : 0;
+    return BAP_OK;
+}
+
+bap_status bap_set_grid_share(bap_option* o, int share) {
+    clear_error();
+    if (!o || share < 1 || share > 64) return fail(BAP_EINVAL, "grid share outside 1..64");
+    o->grid_share = share;
+    return BAP_OK;
+}
+
 bap_status bap_set_unit_paths(bap_option* o, int paths) {
     clear_error();
     if (!o || paths < 0 || paths > 65536 || paths % 32 != 0)
@@ -1399,7 +1483,7 @@ bap_status bap_set_unit_paths(bap_option* o, int paths) {
 
 bap_status bap_set_paths_per_lane(bap_option* o, int ppl) {
     clear_error();
-    if (!o || ppl < 1 || ppl > 2) return fail(BAP_EINVAL, "paths per lane outside 1..2");
+    if (!o || ppl < 0 || ppl > 2) return fail(BAP_EINVAL, "paths per lane outside 0..2");
     o->ppl = ppl;
     return BAP_OK;
 }
@@ -1538,8 +1622,10 @@ bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_
     AllocScope scope(o->stream);
     cudaStream_t st = o->stream;
     const int n_bnd = (o->payoff == BAP_MAX_CALL && d > 1) ? d : 1;
-    const int chunk = choose_chunk(n_items, p->N1, o->unit_paths);
+    const LaunchChoice lc = tuned_launch(d, tune_kind(BAP_METHOD_IZ, o->degree), n_items, p->N1);
+    const int chunk = choose_chunk(n_items, p->N1, o->unit_paths ? o->unit_paths : lc.unit);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
+    o->ppl_fit = lc.ppl;
     TRY(reserve_items(o, n_items, C, p->max_iter));
     DevBuf ds, dp, di, dl;
     TRY(ds.reserve((size_t)n_items * d * 8));

@@ -606,7 +606,11 @@ __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr
         if (isinf(thr[i]) && thr[i] < 0) F0 += alpha[i] * pol[i];
     rf[0] = (float)F0;
     rd[0] = F0;
-    int off = 2 + 2 * nF;
+    auto put_int = [&](int pos, int v) {
+        rf[pos] = __int_as_float(v);
+        rd[pos] = __longlong_as_double((long long)v);
+    };
+    int off = 2 + 4 * nF;
     for (int f = 0; f < nF; ++f) {
         int idx[BAP_MAX_STUMPS];
         int n = 0;
@@ -616,10 +620,10 @@ __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr
                 while (k > 0 && thr[idx[k - 1]] > thr[i]) { idx[k] = idx[k - 1]; --k; }
                 idx[k] = i;
             }
-        rf[2 + f] = __int_as_float(n);
-        rd[2 + f] = __longlong_as_double((long long)n);
-        rf[2 + nF + f] = __int_as_float(off);
-        rd[2 + nF + f] = __longlong_as_double((long long)off);
+        put_int(2 + f, n);
+        put_int(2 + nF + f, off);
+        put_int(2 + 2 * nF + f, 0);
+        put_int(2 + 3 * nF + f, 0);
         if (n == 0) continue;
         double tot = 0.0;
         for (int i = 0; i < n; ++i) tot += alpha[idx[i]] * pol[idx[i]];
@@ -635,6 +639,38 @@ __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr
             if (c < n) pre += alpha[idx[c]] * pol[idx[c]];
         }
         off += 2 * n + 1;
+        // the search grid over [t_0, t_{n-1}]: cell c covers [t_0 + c w, t_0 + (c + 1) w); its word
+        // counts the thresholds below its lower edge minus the margin (lo) and below its upper edge
+        // plus the margin (hi), compared in the precision of each kernel's staged thresholds
+        const int G = cmc_grid_cells(n);
+        const double t0 = thr[idx[0]], t1 = thr[idx[n - 1]];
+        if (G == 0 || !(t1 > t0)) continue;
+        // margin: 1e-4 of a cell, and at least 8 FP32 rounding units of the values compared (the
+        // kernel's cell index a x + b carries about one unit of |x| + |t_0|)
+        const double w = (t1 - t0) / G;
+        const double mg = 1e-4 * w + 8.0 * 1.1920928955078125e-07 * (fabs(t0) + fabs(t1) + w);
+        put_int(2 + 2 * nF + f, G);
+        put_int(2 + 3 * nF + f, off);
+        const double a = G / (t1 - t0), b = -t0 * a - 0.5;
+        rf[off] = (float)a;
+        rd[off] = a;
+        rf[off + 1] = (float)b;
+        rd[off + 1] = b;
+        // the edges grow with c, so each count is a pointer walked once along the sorted
+        // thresholds (FP32 values for the FP32 record, FP64 for the FP64 one)
+        int lf = 0, hf = 0, ld = 0, hd = 0;
+        for (int c = 0; c < G; ++c) {
+            const double lo_edge = c == 0 ? -INFINITY : t0 + c * w - mg;
+            const double hi_edge = c == G - 1 ? INFINITY : t0 + (c + 1) * w + mg;
+            while (lf < n && (double)(float)thr[idx[lf]] < lo_edge) ++lf;
+            while (hf < n && (double)(float)thr[idx[hf]] < hi_edge) ++hf;
+            while (ld < n && thr[idx[ld]] < lo_edge) ++ld;
+            while (hd < n && thr[idx[hd]] < hi_edge) ++hd;
+            rf[off + 2 + c] = __int_as_float(lf | (hf << 16));
+            rd[off + 2 + c] = __longlong_as_double((long long)(ld | (hd << 16)));
+        }
+
+        off += 2 + G;
     }
 }
 

@@ -146,8 +146,10 @@ struct bap_option {
     int grid_share = 1;           // cooperative launches use at most 1/grid_share of the device
     unsigned long long wait_limit_ns = 0;   // grid-barrier wait bound; 0: automatic
     int boost_form = 3;           // CMC boosting: 3 by J, 2 warp per feature, 1 cluster, 0 one block
-    int ppl = 1;                  // path slots per lane of the FP32 quadratic I&Z kernels
-    int unit_paths = 0;           // paths per warp unit of the fits' path launches (0: automatic)
+    int ppl = 0;                  // path slots per lane of the FP32 quadratic I&Z kernels (0: tuned)
+    int ppl_fit = 1;              // the tuned choice for the current fit's Newton launches
+    int unit_paths = 0;           // paths per warp unit of the fits' path launches (0: tuned)
+    int last_unit = 0;            // paths per unit the last fit ran with
     int last_boost_form = 0;      // form the last CMC fit ran
     cudaGraphExec_t graph_exec = nullptr;
     bap_iz_params graph_params{};

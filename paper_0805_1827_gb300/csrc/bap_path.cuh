@@ -557,20 +557,34 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                             const Real* rec = rule_rows + kr * a.rule_stride;
                             Real F = rec[0];
 #pragma unroll
+                            auto rec_int = [&](int pos) -> int {
+                                if constexpr (sizeof(Real) == 4) return __float_as_int((float)rec[pos]);
+                                else return (int)__double_as_longlong((double)rec[pos]);
+                            };
                             for (int f = 0; f < NF; ++f) {
-                                int nf, off;
-                                if constexpr (sizeof(Real) == 4) {
-                                    nf = __float_as_int((float)rec[2 + f]);
-                                    off = __float_as_int((float)rec[2 + NF + f]);
-                                } else {
-                                    nf = (int)__double_as_longlong((double)rec[2 + f]);
-                                    off = (int)__double_as_longlong((double)rec[2 + NF + f]);
-                                }
+                                const int nf = rec_int(2 + f);
+                                const int off = rec_int(2 + NF + f);
                                 if (nf > 0) {
                                     Real xv = phi;
 #pragma unroll
                                     for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
                                     int lo = 0, hi = nf;
+                                    const int G = rec_int(2 + 2 * NF + f);
+                                    if (G > 0) {
+                                        // the cell of x bounds the count to [lo, hi]
+                                        const int goff = rec_int(2 + 3 * NF + f);
+                                        Real u = fma(rec[goff], xv, rec[goff + 1]);
+                                        u = fmin(fmax(u, (Real)0), (Real)(G - 1));
+                                        int c;
+                                        if constexpr (sizeof(Real) == 4)
+                                            c = __float_as_int(u + 12582912.0f) - 0x4B400000;
+                                        else
+                                            c = (int)(__double_as_longlong(u + 6755399441055744.0) -
+                                                      0x4338000000000000LL);
+                                        const int wgrid = rec_int(goff + 2 + c);
+                                        lo = wgrid & 0xffff;
+                                        hi = wgrid >> 16;
+                                    }
                                     while (lo < hi) {
                                         const int mid = (lo + hi) >> 1;
                                         if (rec[off + mid] < xv) lo = mid + 1; else hi = mid;

@@ -276,3 +276,37 @@ def test_fp64_continuation_is_the_oracle_and_states_the_fp32_error():
     print("fp32 error of the continuation estimates: max", rel32.max(), "median", np.median(rel32))
     assert rel32.max() <= 1e-4
     opt.close()
+
+
+@pytest.mark.parametrize("spread", [40.0, 1e-3])
+def test_cmc_rule_search_grid_on_clustered_thresholds(spread):
+    """The stump rule's per-feature search grid returns exactly the binary search's count, also
+    when a feature's thresholds are many and clustered far from zero (cells narrower than the
+    FP32 rounding of the cell index would be without its margins): 256 stumps on the first
+    price, thresholds spread over `spread` around 100, against the oracle's plain stump sum."""
+    from bap_workloads import OptionSpec, equicorrelation
+    spec = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.25], delta=[0.0, 0.0],
+                      rho=equicorrelation(2, 0.2), r=0.05, K=100.0, T=1.0, n_dates=4,
+                      payoff="basket_put")
+    rules = oracle.empty_cmc_rules(spec, 256)
+    rng = np.random.default_rng(5)
+    for m in (2, 3):
+        rules.n_stumps[m] = 256
+        rules.feat[m, :] = 0
+        rules.thr[m, :] = 100.0 + spread * (rng.random(256) - 0.5)
+        rules.pol[m, :] = np.where(rng.random(256) < 0.5, 1, -1)
+        rules.alpha[m, :] = 0.01 + 0.1 * rng.random(256)
+        rules.fitted[m] = 1
+    opt = bap.Option(spec)
+    opt.import_rules(to_buffer(rules))
+    starts = np.array([[100.0 + spread * v, 100.0] for v in np.linspace(-0.4, 0.4, 9)])
+    ids = np.arange(len(starts))
+    N = 4000
+    g, _ = opt.debug_continuation(1, PURPOSE_CMC, 3, ids, starts, N)
+    o, _ = oracle.continuation(spec, rules, 1, PURPOSE_CMC, 3, ids, starts, N)
+    for i in range(len(starts)):
+        Cg, Co = g[i, 0] / N, o[i, 0] / N
+        if abs(Cg - Co) > c_tol(Co, spec.K, N):
+            nf, dC, corrected = replay(opt, spec, rules, 1, PURPOSE_CMC, 3, i, starts[i], N)
+            assert nf > 0 and abs(corrected - Co) <= c_tol(Co, spec.K, N), (i, Cg, Co)
+    opt.close()
