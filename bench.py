@@ -718,7 +718,8 @@ def run_ours(args) -> None:
                           "source": "autotuner table compiled into the library "
                                     "(paper_0805_1827_gb300/csrc/bap_tuning.inc)"},
         "prices": {f"S0={s0:g}": {"price": r["price"], "se": r["se"],
-                                  "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"]}
+                                  "fp64_delta": r["fp64_delta"], "n_noconv": r["n_noconv"],
+                                  "fit_path_steps": r["fit_path_steps"]}
                    for s0, r in zip(S0S, last)},
     }
     if args.serving > 0:
