@@ -322,7 +322,8 @@ __global__ void stage_iz_kernel(const double* coef64, int n_dates, int n_bnd, in
 // [reg] Least squares of x/K on the polynomial basis of y/K for boundary b of date m (FP64).
 // Points with status "no root" are left out; fewer points than coefficients -> degree 0 (their
 // mean); no points -> "never exercise".  Normal equations on the diagonally equilibrated Gram
-// matrix, solved by Cholesky; a Cholesky failure also falls back to the mean.
+// matrix, solved by Cholesky and corrected by one refinement step on the residual; a Cholesky
+// failure also falls back to the mean.
 
 __device__ inline double basis_val(const double* y, int bi, int bj, int bk) {
     const double a = bi < 0 ? 1.0 : y[bi];
@@ -519,6 +520,61 @@ __global__ void __launch_bounds__(kLsThreads) ls_fit_kernel(const DevModel* M, i
                     coef[i] = v / G[i * P + i];
                 }
                 for (int i = 0; i < P; ++i) coef[i] *= dsc[i];
+            }
+            __syncthreads();
+            // One step of refinement with the same factor (corrected semi-normal equations,
+            // Bjorck): the residual r = x - A c of the used points in FP64, then A^T r solved as
+            // above and added to c.  Normal equations alone leave a forward error of order
+            // cond(A)^2 u; the corrected step brings it to order cond(A) u, as a QR
+            // factorisation of A would, for cond(A)^2 u < 1.
+            double gacc = 0.0;                    // thread i < P: entry i of A^T r, point order
+            for (int j0 = 0; j0 < J; j0 += kChunk) {
+                for (int t = threadIdx.x; t < kChunk; t += blockDim.x) {
+                    const int j = j0 + t;
+                    int used = 0;
+                    if (j < J) {
+                        const int item = b * J + j;
+                        if (state[item].status != ST_NOROOT) {
+                            used = 1;
+                            const double* S = start + (size_t)item * d;
+                            double y[MAXD];
+                            int u = 0;
+                            for (int q = 0; q < d; ++q)
+                                if (q != p) y[u++] = S[q] / K;
+                            double r = state[item].x / K;
+                            for (int i = 0; i < P; ++i) {
+                                const double bv = basis_val(y, bi[i], bj[i], bk[i]);
+                                Bs[t][i] = bv;
+                                r -= coef[i] * bv;
+                            }
+                            Bs[t][P] = r;
+                        }
+                    }
+                    Bu[t] = used;
+                }
+                __syncthreads();
+                if (tid < P)
+                    for (int t = 0; t < kChunk; ++t)
+                        if (Bu[t]) gacc += Bs[t][tid] * Bs[t][P];
+                __syncthreads();
+            }
+            if (tid < P) rhs[tid] = gacc * dsc[tid];
+            __syncthreads();
+            for (int k = 0; k < P; ++k) {
+                if (tid == 0) rhs[k] = rhs[k] / G[k * P + k];
+                __syncthreads();
+                const double zk = rhs[k];
+                for (int i = k + 1 + tid; i < P; i += nth) rhs[i] -= G[i * P + k] * zk;
+                __syncthreads();
+            }
+            if (tid == 0) {
+                double dlt[MAXCOEF];
+                for (int i = P - 1; i >= 0; --i) {
+                    double v = rhs[i];
+                    for (int k = i + 1; k < P; ++k) v -= G[k * P + i] * dlt[k];
+                    dlt[i] = v / G[i * P + i];
+                }
+                for (int i = 0; i < P; ++i) coef[i] += dlt[i] * dsc[i];
             }
         } else if (tid == 0) {
             for (int i = 0; i < P; ++i) coef[i] = 0.0;

@@ -190,13 +190,14 @@ def compare_ls(opt, spec, degree, J, starts, x, st, coef_o):
         fit_o = A @ coef_o[b]
         scale = max(1.0, float(np.abs(x[sl][use] / K).max()))
         # the device solves the normal equations (Cholesky of the Gram matrix scaled to a unit
-        # diagonal) in FP64, whose forward error grows with the square of the design's condition
-        # number (Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., Sec. 20.4):
-        # fitted values within 10 kappa^2 u of the points' scale, kappa = cond(A) with A's
-        # columns scaled to unit length, and never looser than needed below 1e-9
+        # diagonal) in FP64 and corrects the solution with one refinement step on the residual
+        # (corrected semi-normal equations), whose forward error is of order cond(A) u like a QR
+        # solution's (Bjorck; Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed.,
+        # Sec. 20.4) while cond(A)^2 u < 1: fitted values within 100 kappa u of the points'
+        # scale, kappa = cond(A) with A's columns scaled to unit length
         Au = A[use]
         kappa = np.linalg.cond(Au / np.linalg.norm(Au, axis=0)) if len(Au) >= A.shape[1] else 1.0
-        tol = max(1e-9, 10.0 * np.finfo(float).eps * kappa * kappa) * scale
+        tol = max(1e-12, 100.0 * np.finfo(float).eps * kappa) * scale
         assert np.max(np.abs(fit_g - fit_o)) <= tol, (b, np.max(np.abs(fit_g - fit_o)), kappa)
     return coef_g
 
