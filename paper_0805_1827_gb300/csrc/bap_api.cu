@@ -125,18 +125,18 @@ bap_status path_blocks_per_sm(const void* fn, int device, size_t smem, int* bps)
     return BAP_OK;
 }
 
-const void* path_fn(int D, int rule, bool fp64, int ppl = 1) {
+const void* path_fn(int D, int rule, bool fp64, int ppl = 1, int payoff = -1) {
     switch (D) {
-        case 1: return path_kernel_fn<1>(rule, fp64, ppl);
-        case 2: return path_kernel_fn<2>(rule, fp64, ppl);
-        case 3: return path_kernel_fn<3>(rule, fp64, ppl);
-        case 4: return path_kernel_fn<4>(rule, fp64, ppl);
-        case 5: return path_kernel_fn<5>(rule, fp64, ppl);
-        case 6: return path_kernel_fn<6>(rule, fp64, ppl);
-        case 7: return path_kernel_fn<7>(rule, fp64, ppl);
-        case 8: return path_kernel_fn<8>(rule, fp64, ppl);
-        case 9: return path_kernel_fn<9>(rule, fp64, ppl);
-        case 10: return path_kernel_fn<10>(rule, fp64, ppl);
+        case 1: return path_kernel_fn<1>(rule, fp64, ppl, payoff);
+        case 2: return path_kernel_fn<2>(rule, fp64, ppl, payoff);
+        case 3: return path_kernel_fn<3>(rule, fp64, ppl, payoff);
+        case 4: return path_kernel_fn<4>(rule, fp64, ppl, payoff);
+        case 5: return path_kernel_fn<5>(rule, fp64, ppl, payoff);
+        case 6: return path_kernel_fn<6>(rule, fp64, ppl, payoff);
+        case 7: return path_kernel_fn<7>(rule, fp64, ppl, payoff);
+        case 8: return path_kernel_fn<8>(rule, fp64, ppl, payoff);
+        case 9: return path_kernel_fn<9>(rule, fp64, ppl, payoff);
+        case 10: return path_kernel_fn<10>(rule, fp64, ppl, payoff);
         default: return nullptr;
     }
 }
@@ -230,7 +230,7 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
     rule = kernel_rule(o, rule);
     // path slots per lane: the option's setting, else the tuned choice of the fit's Newton launches
     const int ppl = o->ppl ? o->ppl : (a.mode == MODE_NEWTON ? o->ppl_fit : 1);
-    const void* fn = path_fn(o->d, rule, fp64, ppl);
+    const void* fn = path_fn(o->d, rule, fp64, ppl, o->payoff);
     if (!fn) return fail(BAP_EINVAL, "no path kernel for d=%d", o->d);
     // the dynamic shared memory the kernel may use (the device's limit less its static arrays)
     size_t max_smem = 0;
@@ -808,9 +808,11 @@ bap_status preload_kernels(int device) {
                 const bool coop = rule == R_NEWTON_COOP || rule == R_NEWTON_COOP3;
                 for (int fp64 = 0; fp64 < (coop ? 1 : 2); ++fp64) {
                     for (int ppl = 1; ppl <= 2; ++ppl) {
-                        const void* fn = path_fn(D, rule, fp64 != 0, ppl);
-                        if (!fn) continue;        // no cubic kernels above MAXD_CUBIC
-                        TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+                        for (int pay = -1; pay <= 2; ++pay) {
+                            const void* fn = path_fn(D, rule, fp64 != 0, ppl, pay);
+                            if (!fn) continue;    // no cubic kernels above MAXD_CUBIC
+                            TRY(raise_smem_limit(fn, device, g_fn[{fn, device}]));
+                        }
                     }
                 }
             }

@@ -82,7 +82,8 @@ __global__ void collect_labels_kernel(const double* label_y, int n, double* x_ou
                                       int* st_out);
 
 // The path kernel of d = D for a rule (or kernel selector), FP32 or FP64, with ppl path slots per
-// lane (2 exists for the FP32 quadratic I&Z kernels; otherwise the ppl = 1 kernel is returned).
-template <int D> const void* path_kernel_fn(int rule, bool fp64, int ppl);
+// lane (2 exists for the FP32 quadratic I&Z kernels; otherwise the ppl = 1 kernel is returned),
+// specialised for the payoff where such a kernel exists (payoff < 0: the general kernel).
+template <int D> const void* path_kernel_fn(int rule, bool fp64, int ppl, int payoff);
 
 }  // namespace bap

@@ -302,7 +302,9 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* err, un
     return ok != 0;
 }
 
-// The path kernel.  Plain form (COOP = false): one pass, `it` = pass_it or *iter_ptr.
+// The path kernel.  PAY >= 0 specialises it for one payoff (the FP32 quadratic I&Z kernels);
+// -1 reads the payoff from the arguments.  Plain form (COOP = false): one pass, `it` = pass_it
+// or *iter_ptr.
 // Cooperative form (COOP = true, I&Z Newton only): every Newton pass of one date in one launch,
 // it = 0, 1, ..., on the same lists, counts and unit counters as the plain form (all zero
 // before the launch); a grid barrier ends each pass, after which all blocks read the same next
@@ -310,7 +312,7 @@ __device__ inline bool grid_barrier(unsigned* bar, unsigned target, int* err, un
 // checks that); the barrier's wait is bounded all the same (coop_err, coop_limit_ns).
 // The unit loop is written once, in this kernel body: moved into an inlined device function it
 // compiled measurably slower.
-template <int D, int RULE, typename Real, bool COOP, int PPL = 1>
+template <int D, int RULE, typename Real, bool COOP, int PPL = 1, int PAY = -1>
 __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_kernel(const PathArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // each thread's FP64 partial sums of its unit (kept here rather than in six registers)
@@ -353,8 +355,10 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     const Real K = (Real)a.K;
-    const bool is_put = a.payoff == BAP_BASKET_PUT;
-    const bool is_max = a.payoff == BAP_MAX_CALL;
+    // the payoff: a template constant in the specialised kernels (PAY >= 0), else the argument's
+    const int payoff = PAY >= 0 ? PAY : a.payoff;
+    const bool is_put = payoff == BAP_BASKET_PUT;
+    const bool is_max = payoff == BAP_MAX_CALL;
 
     // The Cholesky factor and the per-step drift are read straight from the kernel parameters
     // (constant bank operands, no registers).
