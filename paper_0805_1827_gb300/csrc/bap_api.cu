@@ -241,9 +241,9 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
         max_smem = fi.max_dyn_smem;
     }
     size_t smem = path_smem_bytes(a, rule, fp64, o->d);
-    if (smem > max_smem && fp64 && rule != R_NONE) {
-        // the FP64 re-run of a table too large to stage (many dates, many coefficients or
-        // stumps): its kernel reads the rule rows from global memory instead
+    if (smem > max_smem && rule != R_NONE) {
+        // a table too large to stage (many dates, many coefficients or stumps; the FP64
+        // re-runs first): the kernel reads the rule rows from global memory instead
         a.rules_global = 1;
         smem = path_smem_bytes(a, rule, fp64, o->d);
     }

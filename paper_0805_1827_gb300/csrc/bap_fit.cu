@@ -654,6 +654,48 @@ __global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int 
 // thresholds sorted ascending and the step table T_f[c] = sum_{i<c} alpha_i pol_i -
 // sum_{i>=c} alpha_i pol_i, so F(S) = F0 + sum_f T_f[#{thresholds < x_f}].
 
+// One feature's block of a staged CMC record (in the record's own precision): the distinct
+// sorted thresholds (equal in that precision merged) and the step value below each and above
+// the last one.  A step value is the sum of the feature's votes at a value just above that many
+// distinct thresholds: stump i votes +pol_i above its threshold and -pol_i at or below it, so
+// with pre = the alpha-weighted votes of the stumps below, the sum is 2 pre - (all of them).
+template <typename Real>
+__device__ void stage_cmc_feature(int f, int n, const int* idx, const double* thr,
+                                  const int* pol, const double* alpha, double tot, Real* rec,
+                                  int& ovf, int& end) {
+    Real* blk = rec + CMC_HEAD + 2 * CMC_SLOTS * f;
+    int U = 0;
+    for (int c = 0; c < n; ++c)
+        if (c == 0 || (Real)thr[idx[c]] != (Real)thr[idx[c - 1]]) ++U;
+    Real* t = blk;
+    Real* T = blk + CMC_SLOTS;
+    if (U >= CMC_SLOTS) {
+        // too many for the block: [offset, U] in it, the values in the overflow area
+        ovf |= 1 << f;
+        put_int_as(blk, end);
+        put_int_as(blk + 1, U);
+        t = rec + end;
+        T = t + U;
+        end += 2 * U + 1;
+    }
+    double pre = 0.0;
+    int u = 0;
+    for (int c = 0; c < n; ++c) {
+        const Real v = (Real)thr[idx[c]];
+        if (c == 0 || v != (Real)thr[idx[c - 1]]) {
+            t[u] = v;
+            T[u] = (Real)(2.0 * pre - tot);
+            ++u;
+        }
+        pre += alpha[idx[c]] * pol[idx[c]];
+    }
+    T[U] = (Real)(2.0 * pre - tot);
+    if (U < CMC_SLOTS) {
+        for (int i = U; i < CMC_SLOTS; ++i) t[i] = (Real)INFINITY;
+        for (int i = U + 1; i < CMC_SLOTS; ++i) T[i] = T[U];
+    }
+}
+
 __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr, const int* pol,
                               const double* alpha, int rec_len, float* rf, double* rd) {
     for (int i = 0; i < rec_len; ++i) { rf[i] = 0.f; rd[i] = 0.0; }
@@ -662,12 +704,10 @@ __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr
         if (isinf(thr[i]) && thr[i] < 0) F0 += alpha[i] * pol[i];
     rf[0] = (float)F0;
     rd[0] = F0;
-    auto put_int = [&](int pos, int v) {
-        rf[pos] = __int_as_float(v);
-        rd[pos] = __longlong_as_double((long long)v);
-    };
-    int off = 2 + 4 * nF;
+    int ovf_f = 0, ovf_d = 0;
+    int end_f = CMC_HEAD + 2 * CMC_SLOTS * nF, end_d = end_f;
     for (int f = 0; f < nF; ++f) {
+        // the feature's stumps (constant ones excluded) sorted by threshold, stable
         int idx[BAP_MAX_STUMPS];
         int n = 0;
         for (int i = 0; i < ns; ++i)
@@ -676,58 +716,13 @@ __device__ void stage_cmc_one(int nF, int ns, const int* feat, const double* thr
                 while (k > 0 && thr[idx[k - 1]] > thr[i]) { idx[k] = idx[k - 1]; --k; }
                 idx[k] = i;
             }
-        put_int(2 + f, n);
-        put_int(2 + nF + f, off);
-        put_int(2 + 2 * nF + f, 0);
-        put_int(2 + 3 * nF + f, 0);
-        if (n == 0) continue;
         double tot = 0.0;
         for (int i = 0; i < n; ++i) tot += alpha[idx[i]] * pol[idx[i]];
-        double pre = 0.0;
-        for (int c = 0; c <= n; ++c) {
-            if (c < n) {
-                rf[off + c] = (float)thr[idx[c]];
-                rd[off + c] = thr[idx[c]];
-            }
-            const double T = 2.0 * pre - tot;
-            rf[off + n + c] = (float)T;
-            rd[off + n + c] = T;
-            if (c < n) pre += alpha[idx[c]] * pol[idx[c]];
-        }
-        off += 2 * n + 1;
-        // the search grid over [t_0, t_{n-1}]: cell c covers [t_0 + c w, t_0 + (c + 1) w); its word
-        // counts the thresholds below its lower edge minus the margin (lo) and below its upper edge
-        // plus the margin (hi), compared in the precision of each kernel's staged thresholds
-        const int G = cmc_grid_cells(n);
-        const double t0 = thr[idx[0]], t1 = thr[idx[n - 1]];
-        if (G == 0 || !(t1 > t0)) continue;
-        // margin: 1e-4 of a cell, and at least 8 FP32 rounding units of the values compared (the
-        // kernel's cell index a x + b carries about one unit of |x| + |t_0|)
-        const double w = (t1 - t0) / G;
-        const double mg = 1e-4 * w + 8.0 * 1.1920928955078125e-07 * (fabs(t0) + fabs(t1) + w);
-        put_int(2 + 2 * nF + f, G);
-        put_int(2 + 3 * nF + f, off);
-        const double a = G / (t1 - t0), b = -t0 * a - 0.5;
-        rf[off] = (float)a;
-        rd[off] = a;
-        rf[off + 1] = (float)b;
-        rd[off + 1] = b;
-        // the edges grow with c, so each count is a pointer walked once along the sorted
-        // thresholds (FP32 values for the FP32 record, FP64 for the FP64 one)
-        int lf = 0, hf = 0, ld = 0, hd = 0;
-        for (int c = 0; c < G; ++c) {
-            const double lo_edge = c == 0 ? -INFINITY : t0 + c * w - mg;
-            const double hi_edge = c == G - 1 ? INFINITY : t0 + (c + 1) * w + mg;
-            while (lf < n && (double)(float)thr[idx[lf]] < lo_edge) ++lf;
-            while (hf < n && (double)(float)thr[idx[hf]] < hi_edge) ++hf;
-            while (ld < n && thr[idx[ld]] < lo_edge) ++ld;
-            while (hd < n && thr[idx[hd]] < hi_edge) ++hd;
-            rf[off + 2 + c] = __int_as_float(lf | (hf << 16));
-            rd[off + 2 + c] = __longlong_as_double((long long)(ld | (hd << 16)));
-        }
-
-        off += 2 + G;
+        stage_cmc_feature<float>(f, n, idx, thr, pol, alpha, tot, rf, ovf_f, end_f);
+        stage_cmc_feature<double>(f, n, idx, thr, pol, alpha, tot, rd, ovf_d, end_d);
     }
+    put_int_as(rf + 1, ovf_f);
+    put_int_as(rd + 1, ovf_d);
 }
 
 __global__ void stage_cmc_kernel(int n_dates, int nF, int max_stumps, const int* n_stumps,

@@ -220,30 +220,28 @@ __host__ __device__ constexpr int iz_stride(int d, int degree) {
     return degree >= 3 ? iz_stage_stride3(d) : iz_stage_stride(d);
 }
 
-// CMC staged rule record per date (floats or doubles; counts and offsets stored as integer bit
-// patterns): [0] F0 = sum of the constant stumps' votes, [1] spare, then per feature f four
-// header words: [2+f] n_f stumps, [2+nF+f] offset of its sorted thresholds (the step table
-// T_f[0..n_f] follows them), [2+2nF+f] G_f cells of its search grid (0: none), [2+3nF+f] offset
-// of the grid block [a, b, then G_f words lo | hi << 16].  F(S) = F0 + sum_f T_f[#{thresholds
-// < x_f}].  The grid splits [t_0, t_{n_f - 1}] into G_f cells; the cell of x is the nearest
-// integer to a x + b (b includes the -1/2) clamped to 0..G_f-1, and the cell's word bounds the
-// count: every threshold of index < lo is below the cell's lower edge, every one of index >= hi
-// at or above its upper edge, both widened by a margin larger than the rounding of a x + b, so
-// the count is lo plus the thresholds of lo..hi-1 below x -- exactly the binary search's count,
-// in fewer compares.
-// Length: 2 + 4 nF header words, at most 2 n_f + 1 per feature for thresholds and steps and
-// 2 + G_f (G_f < n_f) for its grid.
-__host__ __device__ inline int cmc_record_len(int nF, int max_stumps) {
-    return 2 + 7 * nF + 3 * max_stumps;
-}
+// CMC staged rule record per date (floats or doubles; integers stored as bit patterns):
+// [0] F0 = sum of the constant stumps' votes, [1] the overflow mask (bit f: feature f has more
+// than CMC_SLOTS - 1 distinct thresholds), [2..3] spare, then one fixed block of 2 CMC_SLOTS
+// values per feature f at CMC_HEAD + 2 CMC_SLOTS f: its distinct sorted thresholds t_f[0..U-1]
+// padded with +inf to CMC_SLOTS, then the step table T_f[0..U] (padded with T_f[U]), where
+// T_f[c] is the sum of the feature's stump votes at a value above exactly c of its distinct
+// thresholds.  F(S) = F0 + sum_f T_f[#{t_f < x_f}]; the count is a fixed five-level binary search
+// within the block, so every value read sits at a constant offset from the record.  A feature
+// with U >= CMC_SLOTS distinct thresholds keeps in its block [offset, U] (its first two
+// values) and its thresholds and U + 1 steps in the overflow area after the blocks.
+// Length: the blocks, and at most 2 U + 1 <= 2 n_f + 1 overflow values per feature; odd, so that
+// the records of different dates start in different shared-memory banks.
+// An integer stored in a float or double record slot as a bit pattern, and read back.
+__device__ __forceinline__ void put_int_as(float* p, int v) { *p = __int_as_float(v); }
+__device__ __forceinline__ void put_int_as(double* p, int v) { *p = __longlong_as_double((long long)v); }
+__device__ __forceinline__ int get_int_as(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int get_int_as(double v) { return (int)__double_as_longlong(v); }
 
-// Grid cells for a feature with n thresholds: none below 4, else the power of two at or above
-// n / 2, at most 32.
-__host__ __device__ inline int cmc_grid_cells(int n) {
-    if (n < 4) return 0;
-    int g = 2;
-    while (g < (n + 1) / 2 && g < 32) g <<= 1;
-    return g;
+constexpr int CMC_SLOTS = 32;
+constexpr int CMC_HEAD = 4;
+__host__ __device__ inline int cmc_record_len(int nF, int max_stumps) {
+    return (CMC_HEAD + 2 * CMC_SLOTS * nF + 2 * max_stumps + nF) | 1;
 }
 
 }  // namespace bap

@@ -225,10 +225,11 @@ template <int D, typename Real, int PPL> constexpr int path_min_blocks() {
     return sizeof(Real) == 8 ? 2 : (PPL > 1 ? (D <= 5 ? 3 : 2) : (D <= 5 ? 4 : (D <= 9 ? 3 : 2)));
 }
 
-// Staged rule rows of a launch from date m: dates m+1..NT-1, plus (quadratic I&Z kernels, which
-// evaluate the boundary on every step without a branch) the row of maturity, never used.
+// Staged rule rows of a launch from date m: dates m+1..NT-1, plus (quadratic I&Z and CMC
+// kernels, which evaluate the rule on every step without a per-lane branch) the row of
+// maturity, whose result is never used.
 __host__ __device__ inline int staged_rule_rows(int rule, int nk) {
-    return (rule == R_IZ || rule == R_NEWTON_COOP) ? nk : nk - 1;
+    return (rule == R_IZ || rule == R_NEWTON_COOP || rule == R_CMC) ? nk : nk - 1;
 }
 
 // Dynamic shared memory of one launch: the staged rule rows first (16-byte aligned), then the
@@ -240,6 +241,39 @@ inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
                           ? (size_t)staged_rule_rows(rule, (int)nk) * (size_t)a.rule_stride : 0) +
                      nk + (a.uniform ? 0 : 2 * nk * (size_t)d);
     return n * (fp64 ? 8 : 4) + nk * sizeof(int);
+}
+
+// The stump rule F(S) of a record in which some feature keeps its thresholds in the overflow
+// area (bit f of ovf): the same sum in the same order, each count taken by a plain binary search
+// (a rare path: features with 32 or more distinct thresholds).  An overflow entry that does not
+// fit the record counts nothing.
+template <int NF, int D, typename Real>
+__device__ __forceinline__ Real cmc_rule_overflow(const Real* rec, int ovf, int stride,
+                                                  const Real (&S)[D], Real phi) {
+    Real F = rec[0];
+#pragma unroll 1
+    for (int f = 0; f < NF; ++f) {
+        Real xv = phi;
+#pragma unroll
+        for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
+        const Real* blk = rec + CMC_HEAD + 2 * CMC_SLOTS * f;
+        const Real* t = blk;
+        int n = CMC_SLOTS;
+        if ((ovf >> f) & 1) {
+            const int off = get_int_as(blk[0]);
+            n = get_int_as(blk[1]);
+            const int base = CMC_HEAD + 2 * CMC_SLOTS * NF;
+            if (n < 0 || n > BAP_MAX_STUMPS || off < base || off > stride - 2 * n - 1) continue;
+            t = rec + off;
+        }
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (t[mid] < xv) lo = mid + 1; else hi = mid;
+        }
+        F += t[(t == blk ? CMC_SLOTS : n) + lo];
+    }
+    return F;
 }
 
 // Loads N consecutive values from 16-byte-aligned shared memory with vector loads.
@@ -320,8 +354,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     constexpr int NF = D + 1;
     constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
-    // rows of dates m+1..NT-1, staged in shared memory (global for an FP64 table too large)
-    const bool rules_global = sizeof(Real) == 8 && a.rules_global != 0;
+    // rows of dates m+1..NT-1, staged in shared memory (read from global memory for a table
+    // too large to stage)
+    const bool rules_global = a.rules_global != 0;
     const int rule_len = (RULE == R_NONE || rules_global) ? 0 : staged_rule_rows(RULE, nk) * a.rule_stride;
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
     Real* sh_disc = sh_rule + rule_len;
@@ -334,8 +369,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     if (RULE != R_NONE) {
         const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
         for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
-        if constexpr (sizeof(Real) == 8)
-            if (rules_global) rule_rows = src;
+        if (rules_global) rule_rows = src;
     }
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         const int k = a.m + 1 + i;
@@ -529,6 +563,30 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                         }
                         const bool exr = is_put ? (sp <= B) : (sp >= B);
                         ex = ex && (at_T || (sh_fit[kr] != 0 && exr));
+                    } else if constexpr (RULE == R_CMC) {
+                        // F(S) = F0 + sum_f T_f[#{t_f < x_f}], for every lane of a warp in which
+                        // some lane needs it (a path in the money before maturity)
+                        const bool need = ex && !at_T && has[s];
+                        if (__any_sync(FULL, need)) {
+                            const Real* rec = rule_rows + kr * a.rule_stride;
+                            Real F = rec[0];
+#pragma unroll
+                            for (int f = 0; f < NF; ++f) {
+                                const Real xv = f < D ? S[f < D ? f : 0] : phi;
+                                // five-level search of the block's CMC_SLOTS sorted values
+                                // (+inf padded): p ends at t_f + #{t_f < x}
+                                const Real* p = rec + CMC_HEAD + 2 * CMC_SLOTS * f;
+#pragma unroll
+                                for (int step = CMC_SLOTS / 2; step >= 1; step >>= 1)
+                                    p = (p[step - 1] < xv) ? p + step : p;
+                                F += p[CMC_SLOTS];
+                            }
+                            const int ovf = get_int_as(rec[1]);
+                            if (ovf != 0) F = cmc_rule_overflow<NF>(rec, ovf, a.rule_stride, S, phi);
+                            ex = ex && (at_T || (sh_fit[kr] != 0 && F > 0));
+                        } else {
+                            ex = ex && at_T;
+                        }
                     } else if (ex && !at_T) {
                         if (RULE == R_NONE || !sh_fit[kr]) {
                             ex = false;
@@ -557,46 +615,6 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                                 }
                             }
                             ex = is_put ? (sp <= B) : (sp >= B);
-                        } else {  // R_CMC: F(S) = F0 + sum_f T_f[#{thresholds < x_f}]
-                            const Real* rec = rule_rows + kr * a.rule_stride;
-                            Real F = rec[0];
-#pragma unroll
-                            auto rec_int = [&](int pos) -> int {
-                                if constexpr (sizeof(Real) == 4) return __float_as_int((float)rec[pos]);
-                                else return (int)__double_as_longlong((double)rec[pos]);
-                            };
-                            for (int f = 0; f < NF; ++f) {
-                                const int nf = rec_int(2 + f);
-                                const int off = rec_int(2 + NF + f);
-                                if (nf > 0) {
-                                    Real xv = phi;
-#pragma unroll
-                                    for (int q = 0; q < D; ++q) xv = (f == q) ? S[q] : xv;
-                                    int lo = 0, hi = nf;
-                                    const int G = rec_int(2 + 2 * NF + f);
-                                    if (G > 0) {
-                                        // the cell of x bounds the count to [lo, hi]
-                                        const int goff = rec_int(2 + 3 * NF + f);
-                                        Real u = fma(rec[goff], xv, rec[goff + 1]);
-                                        u = fmin(fmax(u, (Real)0), (Real)(G - 1));
-                                        int c;
-                                        if constexpr (sizeof(Real) == 4)
-                                            c = __float_as_int(u + 12582912.0f) - 0x4B400000;
-                                        else
-                                            c = (int)(__double_as_longlong(u + 6755399441055744.0) -
-                                                      0x4338000000000000LL);
-                                        const int wgrid = rec_int(goff + 2 + c);
-                                        lo = wgrid & 0xffff;
-                                        hi = wgrid >> 16;
-                                    }
-                                    while (lo < hi) {
-                                        const int mid = (lo + hi) >> 1;
-                                        if (rec[off + mid] < xv) lo = mid + 1; else hi = mid;
-                                    }
-                                    F += rec[off + nf + lo];
-                                }
-                            }
-                            ex = F > 0;
                         }
                     }
                     ex = ex && has[s];
