@@ -303,17 +303,18 @@ def serving_bench(bap, n_req: int, max_inflight: int, budget: int) -> dict:
 
 LAUNCH_MODES = {"plain": 0, "graph": 1, "coop": 2}
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "path_kernel_5d_max_call.md")
-PATH_SOURCE = os.path.join(ROOT, "paper_0805_1827_gb300", "csrc", "bap_path.cuh")
+PATH_SOURCES = [os.path.join(ROOT, "paper_0805_1827_gb300", "csrc", f)
+                for f in ("bap_path.cuh", "bap_internal.cuh")]
 
 
 def profiled_traffic():
     """DRAM bytes (read + write) per launch of the dominant kernel, the cooperative Newton
     launch, as ncu measured them on the full workload (profiles/path_kernel_5d_max_call.md);
-    None when the kernel source changed since that capture."""
+    None when the kernel sources changed since that capture."""
     import hashlib
     try:
         text = open(PROFILE_SUMMARY).read()
-        src = hashlib.sha256(open(PATH_SOURCE, "rb").read()).hexdigest()
+        src = hashlib.sha256(b"".join(open(f, "rb").read() for f in PATH_SOURCES)).hexdigest()
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines()

@@ -279,11 +279,11 @@ def test_fp64_continuation_is_the_oracle_and_states_the_fp32_error():
 
 
 @pytest.mark.parametrize("spread", [40.0, 1e-3])
-def test_cmc_rule_search_grid_on_clustered_thresholds(spread):
-    """The stump rule's per-feature search grid returns exactly the binary search's count, also
-    when a feature's thresholds are many and clustered far from zero (cells narrower than the
-    FP32 rounding of the cell index would be without its margins): 256 stumps on the first
-    price, thresholds spread over `spread` around 100, against the oracle's plain stump sum."""
+def test_cmc_rule_overflow_on_clustered_thresholds(spread):
+    """A feature with far more distinct thresholds than the fixed search block holds (they go to
+    the record's overflow area and a plain binary search): 256 stumps on the first price,
+    thresholds spread over `spread` around 100 (1e-3: many equal in FP32, none in FP64),
+    against the oracle's plain stump sum."""
     from bap_workloads import OptionSpec, equicorrelation
     spec = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.25], delta=[0.0, 0.0],
                       rho=equicorrelation(2, 0.2), r=0.05, K=100.0, T=1.0, n_dates=4,
@@ -308,5 +308,53 @@ def test_cmc_rule_search_grid_on_clustered_thresholds(spread):
         Cg, Co = g[i, 0] / N, o[i, 0] / N
         if abs(Cg - Co) > c_tol(Co, spec.K, N):
             nf, dC, corrected = replay(opt, spec, rules, 1, PURPOSE_CMC, 3, i, starts[i], N)
+            assert nf > 0 and abs(corrected - Co) <= c_tol(Co, spec.K, N), (i, Cg, Co)
+    opt.close()
+
+
+@pytest.mark.parametrize("distinct", [0, 1, 31, 32, 200])
+def test_cmc_rule_blocks_duplicates_and_overflow(distinct):
+    """The stump rule's per-feature search at the edges of its layout: `distinct` distinct
+    thresholds on the first price (up to 31 fill the fixed five-level block, 32 and more go to
+    the overflow area), each used twice where room allows; four thresholds on the second price
+    that are equal in FP32 but not in FP64; three on the payoff feature; a constant stump.
+    Continuation values against the oracle's plain stump sum, decision flips replayed."""
+    from bap_workloads import OptionSpec, equicorrelation
+    spec = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.25], delta=[0.0, 0.0],
+                      rho=equicorrelation(2, 0.2), r=0.05, K=100.0, T=1.0, n_dates=4,
+                      payoff="basket_put")
+    rules = oracle.empty_cmc_rules(spec, 256)
+    rng = np.random.default_rng(11 + distinct)
+    reps = 2 if distinct <= 32 else 1
+    for m in (2, 3):
+        feats, thrs = [], []
+        for t in np.sort(80.0 + 40.0 * rng.random(distinct)):
+            feats += [0] * reps
+            thrs += [t] * reps
+        feats += [1] * 4
+        thrs += list(100.0 + 2.0 ** -30 * np.arange(4))
+        feats += [2] * 3
+        thrs += [1.0, 5.0, 12.0]
+        feats += [0]
+        thrs += [-np.inf]
+        n = len(feats)
+        assert n <= 256
+        rules.n_stumps[m] = n
+        rules.feat[m, :n] = feats
+        rules.thr[m, :n] = thrs
+        rules.pol[m, :n] = np.where(rng.random(n) < 0.5, 1, -1)
+        rules.alpha[m, :n] = 0.01 + 0.1 * rng.random(n)
+        rules.fitted[m] = 1
+    opt = bap.Option(spec)
+    opt.import_rules(to_buffer(rules))
+    starts = np.array([[100.0 + v, 100.0 - 0.5 * v] for v in np.linspace(-15.0, 15.0, 7)])
+    ids = np.arange(len(starts))
+    N = 4000
+    g, _ = opt.debug_continuation(1, PURPOSE_CMC, 5, ids, starts, N)
+    o, _ = oracle.continuation(spec, rules, 1, PURPOSE_CMC, 5, ids, starts, N)
+    for i in range(len(starts)):
+        Cg, Co = g[i, 0] / N, o[i, 0] / N
+        if abs(Cg - Co) > c_tol(Co, spec.K, N):
+            nf, dC, corrected = replay(opt, spec, rules, 1, PURPOSE_CMC, 5, i, starts[i], N)
             assert nf > 0 and abs(corrected - Co) <= c_tol(Co, spec.K, N), (i, Cg, Co)
     opt.close()
