@@ -21,8 +21,21 @@ from rules_io import to_buffer
 pytestmark = pytest.mark.gpu
 
 
-def test_full_size_5d_last_date_points_match_oracle():
-    spec, params, N = workload_max_call_5d(100.0)
+def _own_rules_price_gate(opt, spec, r, N, seed):
+    """The device's own fitted rules, exported and priced by the oracle on the same counters:
+    the FP32 price within 0.5 SE, the device's FP64 re-run within 0.05 SE."""
+    from rules_io import from_buffer
+    o = oracle.price(spec, from_buffer(opt.export_rules()), N, seed, n_threads=8)
+    assert abs(r["price"] - o["price"]) <= 0.5 * o["se"], (r["price"], o["price"], o["se"])
+    assert abs((r["price"] - r["fp64_delta"]) - o["price"]) <= 0.05 * o["se"]
+
+
+@pytest.mark.parametrize("S0", [90.0, 100.0, 110.0])
+def test_full_size_5d_last_date_points_match_oracle(S0):
+    """5-asset max-call at the benchmark's size (J = 1024, N1 = 1e5, N = 1e6): the last date's
+    points against the oracle's, every date converged, and the price of the device's own fit
+    against the oracle's price under the same (exported) rules."""
+    spec, params, N = workload_max_call_5d(S0)
     opt = bap.Option(spec)
     opt.fit_boundary(params)
     m = spec.n_dates - 1
@@ -42,14 +55,18 @@ def test_full_size_5d_last_date_points_match_oracle():
         means = xm.reshape(5, params.J).mean(axis=1)
         assert means.std() / means.mean() < 0.02, (mm, means)
     r = opt.price(N, 1)
-    euro = max_call_equicorr([100.0] * 5, 100, 0.05, 0.1, 0.2, 0.3, 3.0)
+    euro = max_call_equicorr([S0] * 5, 100, 0.05, 0.1, 0.2, 0.3, 3.0)
     assert r["price"] > euro + 10 * r["se"]
     assert abs(r["fp64_delta"]) < 0.1 * r["se"]
     assert r["n_noconv"] == 0
+    _own_rules_price_gate(opt, spec, r, N, 1)
     opt.close()
 
 
 def test_full_size_cmc_7d_last_date_labels_and_stumps():
+    """7-asset basket put at the benchmark's size (J = 4000, N2 = 2e4, 200 stumps, N = 1e6): the
+    last date's labels and stumps against the oracle's, and the price of the device's own fit
+    against the oracle's price under the same (exported) rules."""
     spec, params, N = workload_basket_put_7d()
     opt = bap.Option(spec)
     opt.fit_classifier(params)
@@ -80,6 +97,7 @@ def test_full_size_cmc_7d_last_date_labels_and_stumps():
             assert abs(ga - a) <= 1e-8 * max(1.0, abs(a)), (i, ga, a)
     r = opt.price(N, 2)
     assert r["price"] > 0 and abs(r["fp64_delta"]) < 0.1 * r["se"]
+    _own_rules_price_gate(opt, spec, r, N, 2)
     opt.close()
 
 
