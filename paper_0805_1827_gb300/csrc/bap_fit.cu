@@ -652,7 +652,8 @@ __global__ void train_points_kernel(const DevModel* M, int m, RoundKeys rk, int 
 // ---------------------------------------------------------------------------------------------
 // CMC rule staging for one date: constant stumps fold into F0; per feature the finite
 // thresholds sorted ascending and the step table T_f[c] = sum_{i<c} alpha_i pol_i -
-// sum_{i>=c} alpha_i pol_i, so F(S) = F0 + sum_f T_f[#{thresholds < x_f}].
+// sum_{i>=c} alpha_i pol_i, so F(S) = F0 + sum_f T_f[#{thresholds < x_f}], kept at the distinct
+// thresholds only (the record layout is described with CMC_SLOTS).
 
 // One feature's block of a staged CMC record (in the record's own precision): the distinct
 // sorted thresholds (equal in that precision merged) and the step value below each and above
