@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, len(srcs)))) as ex:
         results = list(ex.map(compile_one, srcs))
     if verbose:
         for _, err in results:

@@ -1,0 +1,5 @@
+// Path kernels for d = 9 (one translation unit per d, so that nvcc works on them in parallel).
+#include "bap_path_inst.inc"
+namespace bap {
+template const void* path_kernel_fn<9>(int, bool, int, int);
+}
