@@ -243,5 +243,10 @@ constexpr int CMC_HEAD = 4;
 __host__ __device__ inline int cmc_record_len(int nF, int max_stumps) {
     return (CMC_HEAD + 2 * CMC_SLOTS * nF + 2 * max_stumps + nF) | 1;
 }
+// The part of a record a path kernel stages in shared memory: the head and the fixed blocks
+// (the overflow area stays in global memory), padded to an odd row length.
+__host__ __device__ constexpr int cmc_staged_len(int nF) {
+    return (CMC_HEAD + 2 * CMC_SLOTS * nF) | 1;
+}
 
 }  // namespace bap

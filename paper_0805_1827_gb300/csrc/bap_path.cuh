@@ -58,8 +58,8 @@ struct PathArgs {
     int rule_kind;
     const void* rule_src;        // staged rule table (Real), dates 0..n_dates
     int rule_stride;             // Reals per date
-    int rules_global;            // FP64 kernels only: read the rows of dates m+1.. from rule_src
-                                 // (a table too large for shared memory)
+    int rules_global;            // read the rows of dates m+1.. from rule_src (a table too large
+                                 // for shared memory)
     int n_bnd, n_coef, degree;
     const int* fitted;           // n_dates + 1
     // epilogues
@@ -237,16 +237,17 @@ __host__ __device__ inline int staged_rule_rows(int rule, int nk) {
 // "fitted" flags.
 inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
     const size_t nk = (size_t)(a.n_dates - a.m);
+    const size_t row = rule == R_CMC ? (size_t)cmc_staged_len(d + 1) : (size_t)a.rule_stride;
     const size_t n = (rule != R_NONE && !a.rules_global
-                          ? (size_t)staged_rule_rows(rule, (int)nk) * (size_t)a.rule_stride : 0) +
+                          ? (size_t)staged_rule_rows(rule, (int)nk) * row : 0) +
                      nk + (a.uniform ? 0 : 2 * nk * (size_t)d);
     return n * (fp64 ? 8 : 4) + nk * sizeof(int);
 }
 
 // The stump rule F(S) of a record in which some feature keeps its thresholds in the overflow
-// area (bit f of ovf): the same sum in the same order, each count taken by a plain binary search
-// (a rare path: features with 32 or more distinct thresholds).  An overflow entry that does not
-// fit the record counts nothing.
+// area (bit f of ovf), read from the record in global memory: the same sum in the same order,
+// each count taken by a plain binary search (a rare path: features with 32 or more distinct
+// thresholds).  An overflow entry that does not fit the record counts nothing.
 template <int NF, int D, typename Real>
 __device__ __forceinline__ Real cmc_rule_overflow(const Real* rec, int ovf, int stride,
                                                   const Real (&S)[D], Real phi) {
@@ -355,9 +356,10 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     constexpr int P4 = (RULE == R_IZ3) ? iz_stage_stride3(D) : iz_stage_stride(D);
     const int nk = a.n_dates - a.m;                  // dates m+1..NT
     // rows of dates m+1..NT-1, staged in shared memory (read from global memory for a table
-    // too large to stage)
+    // too large to stage); a CMC row is staged without its overflow area, at an odd row length
     const bool rules_global = a.rules_global != 0;
-    const int rule_len = (RULE == R_NONE || rules_global) ? 0 : staged_rule_rows(RULE, nk) * a.rule_stride;
+    const int row_stride = (RULE == R_CMC && !rules_global) ? cmc_staged_len(NF) : a.rule_stride;
+    const int rule_len = (RULE == R_NONE || rules_global) ? 0 : staged_rule_rows(RULE, nk) * row_stride;
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
     Real* sh_disc = sh_rule + rule_len;
     Real* sh_drift = sh_disc + nk;                   // non-uniform dates: [nk][D]
@@ -366,10 +368,20 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
 
     const DevModel* M = a.model;
     const Real* rule_rows = sh_rule;
+    // the global rows of dates m+1.. (a CMC record's overflow area is read there)
+    const Real* rule_src = RULE == R_NONE ? nullptr
+        : reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
     if (RULE != R_NONE) {
-        const Real* src = reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
-        for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = src[i];
-        if (rules_global) rule_rows = src;
+        if (RULE == R_CMC) {
+            constexpr int FIXED = CMC_HEAD + 2 * CMC_SLOTS * NF;
+            for (int i = threadIdx.x; i < rule_len; i += blockDim.x) {
+                const int r = i / row_stride, c = i - r * row_stride;
+                sh_rule[i] = c < FIXED ? rule_src[(size_t)r * a.rule_stride + c] : (Real)0;
+            }
+        } else {
+            for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = rule_src[i];
+        }
+        if (rules_global) rule_rows = rule_src;
     }
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         const int k = a.m + 1 + i;
@@ -551,7 +563,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                         // evaluated on every step without a branch (the staged table has a zero
                         // row for maturity, where only the payoff decides)
                         Real cc[P4];
-                        load_vec<P4>(rule_rows + kr * a.rule_stride + (is_max ? imax : 0) * P4, cc);
+                        load_vec<P4>(rule_rows + kr * row_stride + (is_max ? imax : 0) * P4, cc);
                         Real B = cc[0];
                         int idx = 1;
 #pragma unroll
@@ -568,7 +580,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                         // some lane needs it (a path in the money before maturity)
                         const bool need = ex && !at_T && has[s];
                         if (__any_sync(FULL, need)) {
-                            const Real* rec = rule_rows + kr * a.rule_stride;
+                            const Real* rec = rule_rows + kr * row_stride;
                             Real F = rec[0];
 #pragma unroll
                             for (int f = 0; f < NF; ++f) {
@@ -582,7 +594,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                                 F += p[CMC_SLOTS];
                             }
                             const int ovf = get_int_as(rec[1]);
-                            if (ovf != 0) F = cmc_rule_overflow<NF>(rec, ovf, a.rule_stride, S, phi);
+                            if (ovf != 0)
+                                F = cmc_rule_overflow<NF>(rule_src + (size_t)kr * a.rule_stride, ovf,
+                                                          a.rule_stride, S, phi);
                             ex = ex && (at_T || (sh_fit[kr] != 0 && F > 0));
                         } else {
                             ex = ex && at_T;
@@ -594,7 +608,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                             // the cubic boundary in the d-1 other prices (nested Horner order);
                             // the coefficients are read from shared memory as they are used
                             const int p = is_max ? imax : 0;
-                            const Real* cc = rule_rows + kr * a.rule_stride + (a.n_bnd > 1 ? p : 0) * P4;
+                            const Real* cc = rule_rows + kr * row_stride + (a.n_bnd > 1 ? p : 0) * P4;
                             Real B = cc[0];
                             if constexpr (D > 1) {
                                 Real y[D - 1];
