@@ -169,6 +169,31 @@ int choose_chunk(long long n_items, long long N, int unit_paths = 0) {
     return (int)c;
 }
 
+// The unit of the Newton passes with few items: a power of two, at most an eighth of the main
+// unit, at least 64 paths (0: main units under 512 paths are not cut).
+int tail_chunk_for(int chunk) {
+    if (chunk < 512) return 0;
+    int t = 64;
+    while (t * 2 <= chunk / 8) t *= 2;
+    return t;
+}
+
+// Units per item of the Newton launches at their largest (the tail passes' smaller units).
+int newton_units_max(long long N, int chunk) {
+    const int t = tail_chunk_for(chunk);
+    const long long C = (N + chunk - 1) / chunk;
+    return (int)std::max(C, t ? (N + t - 1) / t : 0LL);
+}
+
+// The tail split of a date's Newton launch: passes whose units number fewer than two per
+// resident warp of the device, or a quarter of the first pass's, run on the smaller units.
+void set_tail_split(const bap_option* o, PathArgs& a) {
+    a.tail_chunk = tail_chunk_for(a.chunk);
+    if (a.tail_chunk == 0) return;
+    a.C_tail = (int)((a.N + a.tail_chunk - 1) / a.tail_chunk);
+    a.tail_units = std::min(2LL * 32 * o->sm_count, (long long)o->n_items * a.C / 4);
+}
+
 // ---- launch configuration from the autotuner's table ------------------------------------------
 // bap_tuning.inc holds, per launch shape measured on the target GPU by the project's autotuner
 // (autotune.py), the fastest paths per warp unit and path slots per lane of the quadratic I&Z
@@ -482,7 +507,8 @@ bap_status enqueue_newton_pass(bap_option* o, const bap_iz_params* p, int m, int
     a.fp_eps = p->fp_eps;
     a.max_iter = p->max_iter;
     a.fixed_point = p->fixed_point;
-    return launch_path(o, a, R_IZ, false, (long long)o->n_items * C);
+    set_tail_split(o, a);
+    return launch_path(o, a, R_IZ, false, (long long)o->n_items * std::max(C, a.C_tail));
 }
 
 // All Newton passes of date m in one cooperative launch (newton_coop_kernel), on the per-pass
@@ -520,7 +546,8 @@ bap_status enqueue_newton_coop(bap_option* o, const bap_iz_params* p, int m, int
     a.fp_eps = p->fp_eps;
     a.max_iter = p->max_iter;
     a.fixed_point = p->fixed_point;
-    return launch_path(o, a, R_NEWTON_COOP, false, (long long)o->n_items * C);
+    set_tail_split(o, a);
+    return launch_path(o, a, R_NEWTON_COOP, false, (long long)o->n_items * std::max(C, a.C_tail));
 }
 
 bap_status enqueue_iz_prologue(bap_option* o, const bap_iz_params* p) {
@@ -998,7 +1025,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     o->ppl_fit = lc.ppl;
     o->last_unit = chunk;
-    TRY(reserve_items(o, n, C, p->max_iter));
+    TRY(reserve_items(o, n, newton_units_max(p->N1, chunk), p->max_iter));
     TRY(o->korobov_a.reserve(8));
     TRY(o->merit.reserve((size_t)(J + 1) * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
@@ -1378,7 +1405,7 @@ size_t estimate_bytes(const bap_model* md, int method, const void* params, int64
         n = nb * (size_t)p->J;
         const int u = choose_chunk((long long)n, p->N1,
                                    tuned_launch(md->d, tune_kind(BAP_METHOD_IZ, p->degree), (long long)n, p->N1).unit);
-        C = (size_t)((p->N1 + u - 1) / u);
+        C = (size_t)newton_units_max(p->N1, u);
         extra = (size_t)(p->J + 1) * 8 + (size_t)(p->max_iter + 2) * 12;
         rules = nd * nb * (size_t)(MAXCOEF + 4) * 20;
     } else {
@@ -1628,7 +1655,7 @@ bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_
     const int chunk = choose_chunk(n_items, p->N1, o->unit_paths ? o->unit_paths : lc.unit);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     o->ppl_fit = lc.ppl;
-    TRY(reserve_items(o, n_items, C, p->max_iter));
+    TRY(reserve_items(o, n_items, newton_units_max(p->N1, chunk), p->max_iter));
     DevBuf ds, dp, di, dl;
     TRY(ds.reserve((size_t)n_items * d * 8));
     TRY(dp.reserve((size_t)n_items * 4));

@@ -35,6 +35,11 @@ struct PathArgs {
     int64_t N;                   // paths per item
     int chunk;                   // paths per unit (multiple of 32)
     int C;                       // units per item
+    // Newton passes with few items (count * C < tail_units) cut each item into C_tail units of
+    // tail_chunk paths instead, so that the few items still spread over the device (0: never).
+    // The choice depends on the pass's item count alone, so every launch form makes it alike.
+    int tail_chunk, C_tail;
+    long long tail_units;
     // Item lists of the passes.  Pass `it` works on the count[it] items list[it & 1][0..) (items
     // 0, 1, ... when that list is null), taking units from the counter work[it]; the Newton
     // epilogue appends the items that go on to list[(it + 1) & 1] at count[it + 1].  Counts and
@@ -426,14 +431,20 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     unsigned active = gridDim.x, bar_target = 0;
     for (;;) {
     // ---- one pass: every unit of the count[it] items of list[it & 1] ----
-    const long long total_units = (long long)__ldcg(a.count + it) * a.C;
+    const int pass_count = __ldcg(a.count + it);
+    int pass_chunk = a.chunk, pass_C = a.C;
+    if (a.tail_chunk > 0 && (long long)pass_count * a.C < a.tail_units) {
+        pass_chunk = a.tail_chunk;
+        pass_C = a.C_tail;
+    }
+    const long long total_units = (long long)pass_count * pass_C;
         while (true) {
             unsigned long long unit_u = 0;
             if (lane == 0) unit_u = atomicAdd(a.work + it, 1ULL);
             const long long unit = (long long)__shfl_sync(FULL, unit_u, 0);
             if (unit >= total_units) break;
-            const int slot = (int)(unit / a.C);
-            const int chunk = (int)(unit - (long long)slot * a.C);
+            const int slot = (int)(unit / pass_C);
+            const int chunk = (int)(unit - (long long)slot * pass_C);
             const int* active = a.list[it & 1];
             const int item = active ? __ldcg(active + slot) : slot;
             if (!bap_check(item >= 0 && item < a.n_items, 1, a.checks)) continue;
@@ -455,8 +466,8 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             // The unit covers paths n_begin .. n_begin + n_count - 1.  Inside the loop only the
             // 32-bit offset nl moves: counter word 0 is (n_begin + nl) mod 2^32 and word 1 stays
             // item + n_begin / 2^32 (a unit never straddles a multiple of 2^32 paths).
-            const long long n_begin = (long long)chunk * a.chunk;
-            const int n_count = (int)min((long long)a.chunk, (long long)a.N - n_begin);
+            const long long n_begin = (long long)chunk * pass_chunk;
+            const int n_count = (int)min((long long)pass_chunk, (long long)a.N - n_begin);
             const uint32_t w0_base = (uint32_t)n_begin;
             const uint32_t w1_word = (a.ctr_item ? (uint32_t)a.ctr_item[item] : 0u) + (uint32_t)(n_begin >> 32);
 
@@ -697,14 +708,14 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             }
             int last = 0;
             if (lane == 0) {
-                const size_t o = (size_t)item * a.C + chunk;
-                bap_check(chunk >= 0 && chunk < a.C, 4, a.checks);
+                const size_t o = (size_t)item * pass_C + chunk;
+                bap_check(chunk >= 0 && chunk < pass_C, 4, a.checks);
                 a.partial[3 * o + 0] = s0;
                 a.partial[3 * o + 1] = s1;
                 a.partial[3 * o + 2] = s2;
                 a.partial_steps[o] = steps64;
                 __threadfence();
-                last = atomicAdd(&a.done[item], 1) == a.C - 1;
+                last = atomicAdd(&a.done[item], 1) == pass_C - 1;
             }
             last = __shfl_sync(FULL, last, 0);
             if (!last) continue;
@@ -713,8 +724,8 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             __threadfence();
             double t0 = 0, t1 = 0, t2 = 0;
             long long ts = 0;
-            for (int c = lane; c < a.C; c += 32) {
-                const size_t o = (size_t)item * a.C + c;
+            for (int c = lane; c < pass_C; c += 32) {
+                const size_t o = (size_t)item * pass_C + c;
                 t0 += __ldcg(a.partial + 3 * o + 0);
                 t1 += __ldcg(a.partial + 3 * o + 1);
                 t2 += __ldcg(a.partial + 3 * o + 2);
@@ -762,7 +773,8 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     if (next_count == 0 || it + 1 >= a.max_iter) break;
     // blocks beyond what the next pass's units can occupy leave, so that their SMs serve other
     // work (every block reads the same count, so all agree on who stays)
-    const long long need = ((long long)next_count * a.C + (blockDim.x / 32) - 1) / (blockDim.x / 32);
+    const int next_C = (a.tail_chunk > 0 && (long long)next_count * a.C < a.tail_units) ? a.C_tail : a.C;
+    const long long need = ((long long)next_count * next_C + (blockDim.x / 32) - 1) / (blockDim.x / 32);
     if (need < (long long)active) active = (unsigned)need;
     if (blockIdx.x >= active) break;
     ++it;
