@@ -272,6 +272,7 @@ bap_status launch_path(bap_option* o, PathArgs& a, int rule, bool fp64, long lon
         a.rules_global = 1;
         smem = path_smem_bytes(a, rule, fp64, o->d);
     }
+    a.row_stride = path_row_stride(a, rule, o->d);
     if (smem > max_smem) return fail(BAP_EINVAL, "rule tables too large for shared memory (%zu B)", smem);
     int bps = 1;
     TRY(path_blocks_per_sm(fn, o->device, smem, &bps));

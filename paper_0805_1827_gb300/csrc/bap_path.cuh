@@ -65,6 +65,7 @@ struct PathArgs {
     int rule_stride;             // Reals per date
     int rules_global;            // read the rows of dates m+1.. from rule_src (a table too large
                                  // for shared memory)
+    int row_stride;              // Reals per staged row (set by launch_path: path_row_stride)
     int n_bnd, n_coef, degree;
     const int* fitted;           // n_dates + 1
     // epilogues
@@ -237,12 +238,18 @@ __host__ __device__ inline int staged_rule_rows(int rule, int nk) {
     return (rule == R_IZ || rule == R_NEWTON_COOP || rule == R_CMC) ? nk : nk - 1;
 }
 
+// Reals per row of the rule rows a kernel reads: a staged CMC row holds the record without its
+// overflow area; every other row, and any row read from global memory, is the whole record.
+inline int path_row_stride(const PathArgs& a, int rule, int d) {
+    return (rule == R_CMC && !a.rules_global) ? cmc_staged_len(d + 1) : a.rule_stride;
+}
+
 // Dynamic shared memory of one launch: the staged rule rows first (16-byte aligned), then the
 // discount factors, the per-date stepping constants (non-uniform dates only) and the per-date
 // "fitted" flags.
 inline size_t path_smem_bytes(const PathArgs& a, int rule, bool fp64, int d) {
     const size_t nk = (size_t)(a.n_dates - a.m);
-    const size_t row = rule == R_CMC ? (size_t)cmc_staged_len(d + 1) : (size_t)a.rule_stride;
+    const size_t row = (size_t)path_row_stride(a, rule, d);
     const size_t n = (rule != R_NONE && !a.rules_global
                           ? (size_t)staged_rule_rows(rule, (int)nk) * row : 0) +
                      nk + (a.uniform ? 0 : 2 * nk * (size_t)d);
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     // rows of dates m+1..NT-1, staged in shared memory (read from global memory for a table
     // too large to stage); a CMC row is staged without its overflow area, at an odd row length
     const bool rules_global = a.rules_global != 0;
-    const int row_stride = (RULE == R_CMC && !rules_global) ? cmc_staged_len(NF) : a.rule_stride;
+    const int row_stride = a.row_stride;
     const int rule_len = (RULE == R_NONE || rules_global) ? 0 : staged_rule_rows(RULE, nk) * row_stride;
     Real* sh_rule = reinterpret_cast<Real*>(smem_raw);
     Real* sh_disc = sh_rule + rule_len;
@@ -377,12 +384,12 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
     const Real* rule_src = RULE == R_NONE ? nullptr
         : reinterpret_cast<const Real*>(a.rule_src) + (size_t)(a.m + 1) * a.rule_stride;
     if (RULE != R_NONE) {
-        if (RULE == R_CMC) {
+        if (RULE == R_CMC && !rules_global) {
             constexpr int FIXED = CMC_HEAD + 2 * CMC_SLOTS * NF;
-            for (int i = threadIdx.x; i < rule_len; i += blockDim.x) {
-                const int r = i / row_stride, c = i - r * row_stride;
-                sh_rule[i] = c < FIXED ? rule_src[(size_t)r * a.rule_stride + c] : (Real)0;
-            }
+            const int rows = staged_rule_rows(RULE, nk);
+            for (int r = 0; r < rows; ++r)
+                for (int c = threadIdx.x; c < row_stride; c += blockDim.x)
+                    sh_rule[r * row_stride + c] = c < FIXED ? rule_src[(size_t)r * a.rule_stride + c] : (Real)0;
         } else {
             for (int i = threadIdx.x; i < rule_len; i += blockDim.x) sh_rule[i] = rule_src[i];
         }
@@ -605,9 +612,11 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
                                 F += p[CMC_SLOTS];
                             }
                             const int ovf = get_int_as(rec[1]);
-                            if (ovf != 0)
-                                F = cmc_rule_overflow<NF>(rule_src + (size_t)kr * a.rule_stride, ovf,
-                                                          a.rule_stride, S, phi);
+                            if (ovf != 0) {
+                                const Real* rec_g = reinterpret_cast<const Real*>(a.rule_src) +
+                                                    (size_t)(a.m + 1 + kr) * a.rule_stride;
+                                F = cmc_rule_overflow<NF>(rec_g, ovf, a.rule_stride, S, phi);
+                            }
                             ex = ex && (at_T || (sh_fit[kr] != 0 && F > 0));
                         } else {
                             ex = ex && at_T;
