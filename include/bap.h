@@ -97,7 +97,8 @@ typedef struct bap_iz_params {
     double fp_eps;
     int warm_start;           /* 1: each boundary point starts at the later date's fitted boundary
                                  value K B_{m+1}(S_{-p}/K) when that lies inside its initial
-                                 bracket (the paper's "approximate points" refined by Newton);
+                                 bracket (a starting point for Newton, which the paper leaves
+                                 open);
                                  0: at the edge of the bracket (max(K, max S_{-p}) for the
                                  max-call); same results to the convergence tolerances */
 } bap_iz_params;
@@ -112,7 +113,7 @@ typedef struct bap_cmc_params {
                                  per date; 1 one set of J points walked back from the last
                                  fitted date by a Brownian bridge (Section 3.3), each date's
                                  bridge normals being those the independent draw would use */
-    int boost;                /* classifier (Section 3.2: "AdaBoost or LogitBoost"): 0 discrete
+    int boost;                /* classifier (Section 3.2 allows either): 0 discrete
                                  AdaBoost on stumps; 1 LogitBoost with regression stumps (then
                                  n_stumps counts rounds, 1..BAP_MAX_STUMPS/2, each stored as a
                                  threshold stump and a constant; J <= 4096; runs on a cluster of

@@ -327,7 +327,7 @@ def summarize(s0: float, s1: float, N: int, steps: int) -> dict:
 
 
 # ----------------------------------------------------------------------------------------------
-# [glp]: Korobov rank-1 lattice (Section 2.3 "Good Lattice Points").
+# [glp]: Korobov rank-1 lattice (Section 2.3: the initial points are good lattice points).
 
 def p2_merit(J: int, g) -> float:
     """P_2 figure of merit of the rank-1 lattice {j g / J}: -1 + (1/J) sum_j prod_k
@@ -385,7 +385,8 @@ def lattice_points(spec: OptionSpec, m: int, pivot: int, J: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------------
-# [reg]: least-squares boundary regression (Section 2.2, "regression of a quadratic or cubic").
+# [reg]: least-squares boundary regression (Section 2.2: a quadratic or cubic polynomial fitted to
+# the boundary points).
 
 def n_basis(s: int, degree: int) -> int:
     n = 1

@@ -63,7 +63,7 @@ struct IterState {
     int pad[3];
 };
 
-// Newton state of one I&Z boundary point (FP64, Section 2.3 "Newton's iterations").
+// Newton state of one I&Z boundary point (FP64, the Newton iterations of Section 2.3).
 struct ItemState {
     double x, lo, hi, dx_old, dx;
     int iters, status, done, pivot;

@@ -1,9 +1,9 @@
 // bap_path.cuh -- the nested Monte Carlo path kernel (the hot path).
 //
 // One launch evaluates continuation sums for a list of items (I&Z boundary points or their
-// Newton iterates, CMC training points, or the single pricing start point).  Section 2.2:
-// "these optimal boundary points are computed using N_1 MC simulations"; Section 3.2: "From
-// each price point, another N_2 paths are simulated ... to compute the small BA option price".
+// Newton iterates, CMC training points, or the single pricing start point): Section 2.2 finds
+// each boundary point from N_1 simulated paths, Section 3.2 values each training point by
+// N_2 further paths started from it.
 //
 // Work decomposition: an item's N paths are cut into chunks of `chunk` paths; a (item, chunk)
 // unit belongs to one warp, taken from a device counter (persistent grid).  Inside a warp every
