@@ -307,14 +307,27 @@ PATH_SOURCES = [os.path.join(ROOT, "paper_0805_1827_gb300", "csrc", f)
                 for f in ("bap_path.cuh", "bap_internal.cuh")]
 
 
+def kernel_source_hash() -> str:
+    """SHA-256 of the path kernel's sources with their comments and blank lines removed, so that
+    an edit of comments alone leaves it unchanged."""
+    import hashlib
+    import re
+    code = []
+    for f in PATH_SOURCES:
+        text = open(f, encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code += [line.rstrip() for line in text.splitlines() if line.strip()]
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()
+
+
 def profiled_traffic():
     """DRAM bytes (read + write) per launch of the dominant kernel, the cooperative Newton
     launch, as ncu measured them on the full workload (profiles/path_kernel_5d_max_call.md);
-    None when the kernel sources changed since that capture."""
-    import hashlib
+    None when the kernel's code changed since that capture."""
     try:
         text = open(PROFILE_SUMMARY).read()
-        src = hashlib.sha256(b"".join(open(f, "rb").read() for f in PATH_SOURCES)).hexdigest()
+        src = kernel_source_hash()
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines()
