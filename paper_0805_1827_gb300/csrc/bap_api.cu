@@ -178,20 +178,29 @@ int tail_chunk_for(int chunk) {
     return t;
 }
 
-// Units per item of the Newton launches at their largest (the tail passes' smaller units).
-int newton_units_max(long long N, int chunk) {
-    const int t = tail_chunk_for(chunk);
-    const long long C = (N + chunk - 1) / chunk;
-    return (int)std::max(C, t ? (N + t - 1) / t : 0LL);
+// The tail split of a date's Newton launch over n items: passes whose units number fewer than
+// tail_units (two per resident warp of the device, or a quarter of the first pass's) run on
+// the smaller units.
+long long tail_units_for(long long n, int C, int sm_count) {
+    return std::min(2LL * 32 * sm_count, n * C / 4);
 }
 
-// The tail split of a date's Newton launch: passes whose units number fewer than two per
-// resident warp of the device, or a quarter of the first pass's, run on the smaller units.
 void set_tail_split(const bap_option* o, PathArgs& a) {
     a.tail_chunk = tail_chunk_for(a.chunk);
     if (a.tail_chunk == 0) return;
     a.C_tail = (int)((a.N + a.tail_chunk - 1) / a.tail_chunk);
-    a.tail_units = std::min(2LL * 32 * o->sm_count, (long long)o->n_items * a.C / 4);
+    a.tail_units = tail_units_for(o->n_items, a.C, o->sm_count);
+}
+
+// Unit-partial slots of the Newton launches over n items (slots are numbered by an item's
+// position in its pass's list): n C for a main pass, fewer than tail_units / C items times the
+// tail units per item for a tail pass.
+long long newton_unit_slots(long long n, long long N, int chunk, int sm_count) {
+    const long long C = (N + chunk - 1) / chunk;
+    const int t = tail_chunk_for(chunk);
+    if (t == 0) return n * C;
+    const long long tail_items = std::min(n, tail_units_for(n, (int)C, sm_count) / C + 1);
+    return std::max(n * C, tail_items * ((N + t - 1) / t));
 }
 
 // ---- launch configuration from the autotuner's table ------------------------------------------
@@ -434,7 +443,8 @@ bap_status set_rule_cmc(bap_option* o, int max_stumps) {
 }
 
 // Scratch for n items of N paths each.
-bap_status reserve_items(bap_option* o, int n, int C, int max_iter) {
+// Scratch for n items and `slots` unit partials.
+bap_status reserve_items(bap_option* o, int n, long long slots, int max_iter) {
     const int d = o->d;
     TRY(o->start.reserve((size_t)n * d * 8));
     TRY(o->l0f.reserve((size_t)n * d * 4));
@@ -445,8 +455,8 @@ bap_status reserve_items(bap_option* o, int n, int C, int max_iter) {
     TRY(o->active1.reserve((size_t)n * 4));
     TRY(o->counts.reserve((size_t)(max_iter + 2) * 4));
     TRY(o->work.reserve((size_t)(max_iter + 2) * 8));
-    TRY(o->partial.reserve((size_t)n * C * 3 * 8));
-    TRY(o->partial_steps.reserve((size_t)n * C * 8));
+    TRY(o->partial.reserve((size_t)slots * 3 * 8));
+    TRY(o->partial_steps.reserve((size_t)slots * 8));
     TRY(o->done.reserve((size_t)n * 4));
     TRY(o->out_sums.reserve((size_t)n * 3 * 8));
     TRY(o->out_steps.reserve((size_t)n * 8));
@@ -1026,7 +1036,7 @@ bap_status enqueue_fit_iz(bap_option* o, const bap_iz_params* p) {
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     o->ppl_fit = lc.ppl;
     o->last_unit = chunk;
-    TRY(reserve_items(o, n, newton_units_max(p->N1, chunk), p->max_iter));
+    TRY(reserve_items(o, n, newton_unit_slots(n, p->N1, chunk, o->sm_count), p->max_iter));
     TRY(o->korobov_a.reserve(8));
     TRY(o->merit.reserve((size_t)(J + 1) * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
@@ -1275,7 +1285,7 @@ bap_status enqueue_fit_cmc(bap_option* o, const bap_cmc_params* p) {
     o->last_unit = chunk;
     const int C = (int)((p->N2 + chunk - 1) / chunk);
     const int d = o->d;
-    TRY(reserve_items(o, n, C, 1));
+    TRY(reserve_items(o, n, (long long)n * C, 1));
     TRY(reserve_boost(o, J));
     if (p->sampler == 1) TRY(o->bridge_w.reserve((size_t)J * d * 8));
     TRY(o->diag_x.reserve((size_t)(o->n_dates + 1) * n * 8));
@@ -1399,14 +1409,15 @@ bap_status finish_price(bap_option* o, bap_result* res) {
 
 size_t estimate_bytes(const bap_model* md, int method, const void* params, int64_t n_paths) {
     const size_t d = (size_t)md->d, nd = (size_t)md->n_dates + 1;
-    size_t n = 0, C = 0, extra = 0, rules = 0;
+    size_t n = 0, slots = 0, extra = 0, rules = 0;
     if (method == BAP_METHOD_IZ) {
         const bap_iz_params* p = static_cast<const bap_iz_params*>(params);
         const size_t nb = (md->payoff == BAP_MAX_CALL && md->d > 1) ? d : 1;
         n = nb * (size_t)p->J;
         const int u = choose_chunk((long long)n, p->N1,
                                    tuned_launch(md->d, tune_kind(BAP_METHOD_IZ, p->degree), (long long)n, p->N1).unit);
-        C = (size_t)newton_units_max(p->N1, u);
+        // the tail passes' slots bounded without the device's SM count
+        slots = (size_t)newton_unit_slots((long long)n, p->N1, u, 1 << 20);
         extra = (size_t)(p->J + 1) * 8 + (size_t)(p->max_iter + 2) * 12;
         rules = nd * nb * (size_t)(MAXCOEF + 4) * 20;
     } else {
@@ -1414,13 +1425,15 @@ size_t estimate_bytes(const bap_model* md, int method, const void* params, int64
         n = (size_t)p->J;
         const int u = choose_chunk((long long)n, p->N2,
                                    tuned_launch(md->d, tune_kind(BAP_METHOD_CMC, 0), (long long)n, p->N2).unit);
-        C = (size_t)((p->N2 + u - 1) / u);
+        slots = n * (size_t)((p->N2 + u - 1) / u);
         extra = (d + 1) * n * 20 + d * n * 8;     // sorted features, bridge state
-        rules = nd * (size_t)p->n_stumps * (p->boost == 1 ? 2 : 1) * 64;
+        // stumps (feature, threshold, polarity, alpha) and the FP32 + FP64 staged records
+        const size_t ms = (size_t)p->n_stumps * (p->boost == 1 ? 2 : 1);
+        rules = nd * (ms * 24 + (size_t)cmc_record_len((int)d + 1, (int)ms) * 12);
     }
-    const size_t items = n * (d * 8 + sizeof(ItemState) + 40) + n * C * 32 + nd * n * 16;
+    const size_t items = n * (d * 8 + sizeof(ItemState) + 40) + slots * 32 + nd * n * 16;
     const size_t price_c = (size_t)((n_paths + choose_chunk(1, n_paths) - 1) / choose_chunk(1, n_paths));
-    return sizeof(DevModel) + items + extra + rules + std::max(price_c, C * n) * 32 + (1 << 16);
+    return sizeof(DevModel) + items + extra + rules + std::max(price_c, slots) * 32 + (1 << 16);
 }
 
 }  // namespace bap
@@ -1656,7 +1669,7 @@ bap_status bap_debug_newton(bap_option* o, const bap_iz_params* p, int m, int n_
     const int chunk = choose_chunk(n_items, p->N1, o->unit_paths ? o->unit_paths : lc.unit);
     const int C = (int)((p->N1 + chunk - 1) / chunk);
     o->ppl_fit = lc.ppl;
-    TRY(reserve_items(o, n_items, newton_units_max(p->N1, chunk), p->max_iter));
+    TRY(reserve_items(o, n_items, newton_unit_slots(n_items, p->N1, chunk, o->sm_count), p->max_iter));
     DevBuf ds, dp, di, dl;
     TRY(ds.reserve((size_t)n_items * d * 8));
     TRY(dp.reserve((size_t)n_items * 4));

@@ -55,8 +55,9 @@ struct PathArgs {
                                  // the Newton loop (FP32 kernels; nullptr: taken from start)
     const int* ctr_item;         // Philox counter word 1 per item (nullptr: 0)
     const int* pivot;            // pivot asset per item for the pathwise derivative (or nullptr)
-    double* partial;             // items x C x 3
-    long long* partial_steps;    // items x C
+    double* partial;             // per unit 3 sums, at (position in the pass's list) x units
+                                 // per item + unit
+    long long* partial_steps;    // per unit path-steps, same slots
     int* done;                   // per item: units finished in the current pass
     unsigned long long* total_steps;
     // rule
@@ -717,7 +718,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             }
             int last = 0;
             if (lane == 0) {
-                const size_t o = (size_t)item * pass_C + chunk;
+                const size_t o = (size_t)slot * pass_C + chunk;
                 bap_check(chunk >= 0 && chunk < pass_C, 4, a.checks);
                 a.partial[3 * o + 0] = s0;
                 a.partial[3 * o + 1] = s1;
@@ -734,7 +735,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             double t0 = 0, t1 = 0, t2 = 0;
             long long ts = 0;
             for (int c = lane; c < pass_C; c += 32) {
-                const size_t o = (size_t)item * pass_C + c;
+                const size_t o = (size_t)slot * pass_C + c;
                 t0 += __ldcg(a.partial + 3 * o + 0);
                 t1 += __ldcg(a.partial + 3 * o + 1);
                 t2 += __ldcg(a.partial + 3 * o + 2);
