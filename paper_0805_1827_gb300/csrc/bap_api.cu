@@ -445,6 +445,8 @@ bap_status set_rule_cmc(bap_option* o, int max_stumps) {
 // Scratch for n items of N paths each.
 // Scratch for n items and `slots` unit partials.
 bap_status reserve_items(bap_option* o, int n, long long slots, int max_iter) {
+    // the path kernel numbers unit slots in 32 bits
+    if (slots >= (1LL << 32)) return fail(BAP_EINVAL, "too many path units (%lld)", slots);
     const int d = o->d;
     TRY(o->start.reserve((size_t)n * d * 8));
     TRY(o->l0f.reserve((size_t)n * d * 4));

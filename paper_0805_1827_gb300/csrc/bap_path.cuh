@@ -453,6 +453,9 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             if (unit >= total_units) break;
             const int slot = (int)(unit / pass_C);
             const int chunk = (int)(unit - (long long)slot * pass_C);
+            // the unit's partial-sum slot, slot * pass_C + chunk = unit (fewer than 2^32 slots;
+            // the launcher checks): kept instead of slot and chunk, which the epilogue re-derives
+            const unsigned unit_o = (unsigned)unit;
             const int* active = a.list[it & 1];
             const int item = active ? __ldcg(active + slot) : slot;
             if (!bap_check(item >= 0 && item < a.n_items, 1, a.checks)) continue;
@@ -718,8 +721,7 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
             }
             int last = 0;
             if (lane == 0) {
-                const size_t o = (size_t)slot * pass_C + chunk;
-                bap_check(chunk >= 0 && chunk < pass_C, 4, a.checks);
+                const size_t o = unit_o;
                 a.partial[3 * o + 0] = s0;
                 a.partial[3 * o + 1] = s1;
                 a.partial[3 * o + 2] = s2;
@@ -732,10 +734,13 @@ __global__ void __launch_bounds__(256, (path_min_blocks<D, Real, PPL>())) path_k
 
             // ---- the warp that finished the item's last unit: fixed-order sum over its units ----
             __threadfence();
+            const int unit_chunk = (int)(n_begin / pass_chunk);
+            bap_check(unit_chunk >= 0 && unit_chunk < pass_C, 4, a.checks);
+            const size_t o_first = (size_t)unit_o - unit_chunk;    // slot * pass_C
             double t0 = 0, t1 = 0, t2 = 0;
             long long ts = 0;
             for (int c = lane; c < pass_C; c += 32) {
-                const size_t o = (size_t)slot * pass_C + c;
+                const size_t o = o_first + c;
                 t0 += __ldcg(a.partial + 3 * o + 0);
                 t1 += __ldcg(a.partial + 3 * o + 1);
                 t2 += __ldcg(a.partial + 3 * o + 2);
