@@ -14,9 +14,11 @@ from bap_workloads import CMCParams, IZParams, serving_stream, spec_max_call, sp
 pytestmark = pytest.mark.gpu
 
 
-def _fit(spec, params, mode):
+def _fit(spec, params, mode, unit=0):
     o = bap.Option(spec)
     o.set_launch_mode(mode)
+    if unit:
+        o.set_unit_paths(unit)
     if hasattr(params, "N1"):
         o.fit_boundary(params)
     else:
@@ -59,6 +61,27 @@ def test_graph_and_plain_launch_forms_agree():
     c = _fit(spec, p2, bap.LAUNCH_PLAIN)
     assert b.price(50_000, 6)["price"] == c.price(50_000, 6)["price"]
     for o in (a, b, c):
+        o.close()
+
+
+def test_launch_forms_agree_on_the_tail_units():
+    """Newton passes left with few items run on units of an eighth of the main unit; the choice
+    depends on the pass's item count only, so the plain (one launch per pass), graph and
+    cooperative forms still give bitwise the same points, path-steps and price.  2048-path main
+    units over 20000 paths: 10 units per item, 79 of 256 paths in the tail passes."""
+    spec = spec_max_call(3, 100.0, rho=0.2, n_dates=6, T=2.0)
+    params = IZParams(J=32, N1=20_000, degree=2, seed=7)
+    fits = [_fit(spec, params, mode, unit=2048)
+            for mode in (bap.LAUNCH_PLAIN, bap.LAUNCH_GRAPH, bap.LAUNCH_COOP)]
+    for m in range(1, spec.n_dates):
+        ref = fits[0].fit_points(m)
+        for o in fits[1:]:
+            got = o.fit_points(m)
+            assert all(np.array_equal(a, b) for a, b in zip(ref, got)), m
+    r = [o.price(100_000, 5) for o in fits]
+    assert r[0]["price"] == r[1]["price"] == r[2]["price"]
+    assert r[0]["fit_path_steps"] == r[1]["fit_path_steps"] == r[2]["fit_path_steps"]
+    for o in fits:
         o.close()
 
 
