@@ -206,9 +206,10 @@ long long newton_unit_slots(long long n, long long N, int chunk, int sm_count) {
 // ---- launch configuration from the autotuner's table ------------------------------------------
 // bap_tuning.inc holds, per launch shape measured on the target GPU by the project's autotuner
 // (autotune.py), the fastest paths per warp unit and path slots per lane of the quadratic I&Z
-// Newton launches: entries {d, kind 0, items, N, unit paths, slots per lane}.  A fit takes the
-// entry of its d nearest to its shape (log distance in items and paths); without one, the fixed
-// formula of choose_chunk and one slot per lane.
+// Newton launches (kind 0) and the paths per warp unit of the CMC label launches (kind 1):
+// entries {d, kind, items, N, unit paths, slots per lane}.  A fit takes the entry of its kind
+// and d nearest to its shape (log distance in items and paths); without one, the fixed formula
+// of choose_chunk and one slot per lane.
 struct TuneEntry {
     int d, kind, items;
     long long N;
@@ -241,12 +242,13 @@ LaunchChoice tuned_launch(int d, int kind, long long n_items, long long N) {
     return c;
 }
 
-// The tuning kind of a fit: 0 the quadratic (or lower) I&Z Newton launches; the other launches
-// (-1: cubic boundaries, CMC labels) take the formula.  The choice depends on the fit's shape
+// The tuning kind of a fit: 0 the quadratic (or lower) I&Z Newton launches, 1 the CMC label
+// launches; cubic boundaries (-1) take the formula.  The choice depends on the fit's shape
 // only, never on what else runs or on the device share, so a fit's result is the same alone
 // and served.
 int tune_kind(int method, int degree) {
-    return (method == BAP_METHOD_IZ && degree <= 2) ? 0 : -1;
+    if (method == BAP_METHOD_CMC) return 1;
+    return degree <= 2 ? 0 : -1;
 }
 
 // The kernel for a rule: a cubic I&Z boundary has kernels of its own.
