@@ -41,7 +41,7 @@ WORKLOAD = "5-asset max-call Bermudan, I&Z, rho=0.3, J=1024 Korobov, N1=1e5, 9 d
 CPU_J, CPU_N1, CPU_NPRICE = 64, 4000, 100_000
 
 
-def survey_ops_per_path_step(d: int = 5) -> dict:
+def component_ops_per_path_step(d: int = 5) -> dict:
     """Algorithmic 32-bit lane operations of one path-step of the I&Z max-call path, counted
     by component: Philox4x32-10 at ceil(d/4) calls of 10 rounds x (2 mul-hi + 2 mul-lo + 2
     xor) plus the key schedule's bumps (80 per call), Box-Muller at 4 MUFU + 6 FP32 per pair,
@@ -685,7 +685,7 @@ def run_ours(args) -> None:
     rootfind = root_find_study(bap) if args.paper_tables else None
     degrees = boundary_degree_study(bap) if args.paper_tables else None
 
-    ops = survey_ops_per_path_step(5)
+    ops = component_ops_per_path_step(5)
     strict = alg_ops_per_path_step(5, 2)
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
