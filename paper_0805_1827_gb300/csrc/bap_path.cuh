@@ -5,14 +5,15 @@
 // each boundary point from N_1 simulated paths, Section 3.2 values each training point by
 // N_2 further paths started from it.
 //
-// Work decomposition: an item's N paths are cut into chunks of `chunk` paths; a (item, chunk)
-// unit belongs to one warp, taken from a device counter (persistent grid).  Inside a warp every
-// lane runs one path at a time and takes the next path index of the chunk as soon as its path
-// stops (warp ballot), so early-stopped paths leave no idle lanes.  Results per unit are summed
-// per lane (FP32, flushed to FP64 after every block of at most 32 warp steps), reduced across
-// the warp in a fixed shuffle
-// tree and written to a fixed slot; the warp that completes an item's last unit sums the slots
-// in fixed order, so results are bitwise reproducible whatever the scheduling.  That warp then
+// Work decomposition: an item's N paths are cut into chunks of `chunk` paths (Newton passes left
+// with few items: of `tail_chunk` paths); an (item, chunk) unit belongs to one warp, taken from
+// a device counter (persistent grid).  Inside a warp every lane runs one path at a time and
+// takes the next path index of the chunk as soon as its path stops (warp ballot), so
+// early-stopped paths leave no idle lanes.  Results per unit are summed per lane (FP32, flushed
+// to FP64 after every block of at most 32 warp steps), reduced across the warp in a fixed
+// shuffle tree and written to a fixed slot (the item's position in the pass's list times the
+// units per item, plus the unit); the warp that completes an item's last unit sums the slots in
+// fixed order, so results are bitwise reproducible whatever the scheduling.  That warp then
 // runs the item's epilogue on the device: the Newton update of an I&Z boundary point (and its
 // re-queueing), the CMC label, or the plain sums.
 #pragma once
