@@ -312,23 +312,26 @@ def test_cmc_rule_overflow_on_clustered_thresholds(spread):
     opt.close()
 
 
-@pytest.mark.parametrize("distinct", [0, 1, 31, 32, 200])
+@pytest.mark.parametrize("distinct", [0, 1, 31, 32, 200, (31, 32), (200, 0)])
 def test_cmc_rule_blocks_duplicates_and_overflow(distinct):
     """The stump rule's per-feature search at the edges of its layout: `distinct` distinct
     thresholds on the first price (up to 31 fill the fixed five-level block, 32 and more go to
-    the overflow area), each used twice where room allows; four thresholds on the second price
-    that are equal in FP32 but not in FP64; three on the payoff feature; a constant stump.
-    Continuation values against the oracle's plain stump sum, decision flips replayed."""
+    the overflow area; a pair gives the two fitted dates different counts, so that lanes at
+    different dates take different paths), each used twice where room allows; four thresholds
+    on the second price that are equal in FP32 but not in FP64; three on the payoff feature; a
+    constant stump.  Continuation values against the oracle's plain stump sum, decision flips
+    replayed."""
     from bap_workloads import OptionSpec, equicorrelation
     spec = OptionSpec(d=2, S0=[100.0, 100.0], sigma=[0.2, 0.25], delta=[0.0, 0.0],
                       rho=equicorrelation(2, 0.2), r=0.05, K=100.0, T=1.0, n_dates=4,
                       payoff="basket_put")
     rules = oracle.empty_cmc_rules(spec, 256)
-    rng = np.random.default_rng(11 + distinct)
-    reps = 2 if distinct <= 32 else 1
-    for m in (2, 3):
+    per_date = distinct if isinstance(distinct, tuple) else (distinct, distinct)
+    rng = np.random.default_rng(11 + sum(per_date))
+    for m, n_distinct in zip((2, 3), per_date):
+        reps = 2 if n_distinct <= 32 else 1
         feats, thrs = [], []
-        for t in np.sort(80.0 + 40.0 * rng.random(distinct)):
+        for t in np.sort(80.0 + 40.0 * rng.random(n_distinct)):
             feats += [0] * reps
             thrs += [t] * reps
         feats += [1] * 4
