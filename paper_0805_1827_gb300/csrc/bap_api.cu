@@ -1937,7 +1937,8 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
             th[i] = buf[off + 4 * i + 1];
             pl[i] = (int)buf[off + 4 * i + 2];
             al[i] = buf[off + 4 * i + 3];
-            if (f[i] < 0 || f[i] > o->d || (pl[i] != 1 && pl[i] != -1 && al[i] != 0.0))
+            if (f[i] < 0 || f[i] > o->d || (pl[i] != 1 && pl[i] != -1 && al[i] != 0.0) ||
+                std::isnan(th[i]) || !std::isfinite(al[i]))
                 return fail(BAP_EINVAL, "bad stump");
         }
         for (int k = 0; k < nd; ++k) {

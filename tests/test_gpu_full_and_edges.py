@@ -233,6 +233,36 @@ def test_bad_arguments_are_rejected():
     opt.close()
 
 
+def test_imported_stump_rules_are_checked():
+    """A CMC rule imported with a NaN threshold, a non-finite weight, a feature outside 0..d or
+    more stumps than the rule holds is refused (BAP_EINVAL) before anything is staged."""
+    spec = spec_max_call(2, 100.0, n_dates=3, T=1.0)
+    base = oracle.empty_cmc_rules(spec, 4)
+    base.n_stumps[1] = 2
+    base.feat[1, :2] = [0, 2]
+    base.thr[1, :2] = [100.0, 5.0]
+    base.pol[1, :2] = [1, -1]
+    base.alpha[1, :2] = [0.3, 0.2]
+    base.fitted[1] = 1
+    opt = bap.Option(spec)
+    opt.import_rules(to_buffer(base))
+    for field, value in [("thr", np.nan), ("alpha", np.inf), ("feat", 3)]:
+        bad = oracle.empty_cmc_rules(spec, 4)
+        for name in ("n_stumps", "feat", "thr", "pol", "alpha", "fitted"):
+            getattr(bad, name)[...] = getattr(base, name)
+        getattr(bad, field)[1, 0] = value
+        with pytest.raises(bap.BapError) as e:
+            opt.import_rules(to_buffer(bad))
+        assert e.value.status == bap.BAP_EINVAL, field
+    buf = to_buffer(base)
+    nd, ms = spec.n_dates + 1, 4
+    buf[6 + nd + nd * ms * 4 + 1] = ms + 1          # more stumps than the rule holds
+    with pytest.raises(bap.BapError) as e:
+        opt.import_rules(buf)
+    assert e.value.status == bap.BAP_EINVAL
+    opt.close()
+
+
 # ---- edges of the method variants ------------------------------------------------------------
 
 def test_cubic_boundary_at_the_largest_d():
