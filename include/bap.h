@@ -268,7 +268,8 @@ bap_status bap_price(bap_option *opt, int64_t n_paths, uint64_t seed, bap_result
  * n_bnd, degree, n_coef, max_stumps, fitted[n_dates+1], then I&Z coef[(n_dates+1)*n_bnd*n_coef]
  * or CMC per date (n_dates+1) x max_stumps x (feat, thr, pol, alpha) plus n_stumps[n_dates+1]].
  * Import accepts the same layout (kind 0 = exercise at maturity only) and returns EINVAL for a
- * shape that does not match the option, a stump whose feature is outside 0..d, whose polarity is
+ * shape that does not match the option, a boundary coefficient that is not finite, a stump
+ * whose feature is outside 0..d, whose polarity is
  * not +-1 (with a nonzero weight), whose threshold is NaN or whose weight is not finite, or a
  * stump count above max_stumps. */
 bap_status bap_export_rules(const bap_option *opt, double *buf, size_t *len);

@@ -1919,6 +1919,8 @@ bap_status bap_import_rules(bap_option* o, const double* buf, size_t len) {
         if ((int)buf[2] != o->n_bnd || (int)buf[4] != o->n_coef) return fail(BAP_EINVAL, "boundary shape mismatch");
         const size_t nc = (size_t)nd * o->n_bnd * o->n_coef;
         if (len < off + nc) return fail(BAP_EINVAL, "short buffer");
+        for (size_t i = 0; i < nc; ++i)
+            if (!std::isfinite(buf[off + i])) return fail(BAP_EINVAL, "non-finite boundary coefficient");
         CU(cudaMemcpyAsync(o->coef64.p, buf + off, nc * 8, cudaMemcpyHostToDevice, o->stream));
         stage_iz_kernel<<<(nd * o->n_bnd + 127) / 128, 128, 0, o->stream>>>(
             o->coef64.as<double>(), o->n_dates, o->n_bnd, o->n_coef, o->d - 1, o->degree, o->K,

@@ -260,6 +260,13 @@ def test_imported_stump_rules_are_checked():
     with pytest.raises(bap.BapError) as e:
         opt.import_rules(buf)
     assert e.value.status == bap.BAP_EINVAL
+    # and an I&Z boundary with a NaN coefficient
+    iz = oracle.empty_iz_rules(spec, 2)
+    iz.coef[1, 0, 0] = np.nan
+    iz.fitted[1] = 1
+    with pytest.raises(bap.BapError) as e:
+        opt.import_rules(to_buffer(iz))
+    assert e.value.status == bap.BAP_EINVAL
     opt.close()
 
 
